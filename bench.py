@@ -1,0 +1,339 @@
+#!/usr/bin/env python3
+"""Benchmark of the encrypted 1:N iris matching hot path on GB300.
+
+One step = one pass of the whole hot path over one query batch: basis extension of the query
+ciphertext (and its tensor-core planes), the CCMM against the resident encrypted database, and
+the fold.  Workload (Section 6): 32 query eyes x 31 rotations against 7 x 2^14 = 114,688 database
+iris codes, N_db = 2^14, N_q = 2^13, d = 2^14, eight primes below 2^60 (L_q = 2); synthetic
+templates (uniform codes, Bernoulli(0.9) masks, 5% planted noisy copies).  The encrypted database
+(206 GB) is built once before timing and stays resident; it exceeds L2 many times over, so no L2
+flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--form F] [--impl reference]
+
+Prints one JSON line (rank 0).  Under torchrun every rank matches the same query batch against
+its own database of 114,688 codes (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "iris comparisons/s (32 eyes × 7·2^14 DB, 1 GB300), int8-TC vs u64 form; % INT8 peak"
+UNIT = "comparisons/s"
+N_EYES, N_DB = 32, 7 * (1 << 14)
+WORKLOAD = ("paper-shaped CCMM + fold: 32 eyes x 31 rotations vs 114,688 codes (7 blocks of N_db=2^14), "
+            "N_q=2^13, d=2^14, K=24,576, 8 primes < 2^60 (L_q=2), Delta=2^60")
+DTYPE = {"u64": "u64", "i8_digits": "int8", "i8_crt": "int8", "f16_crt": "f16"}
+# DRAM bytes per launch of the dominant kernel from the committed ncu captures (profiles/);
+# None until a capture of the current kernel exists.
+NCU_TRAFFIC = {}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling (200 ms) during the timed region."""
+
+    def __init__(self, dev: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(dev)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except FileNotFoundError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# ------------------------------------------------------------------------------ CPU oracle legs
+
+def oracle_sample(seconds_target: float, seed: int = 0):
+    """Time the oracle on a bounded sample of the same workload: basis extension of the whole
+    query operand, the u128 schoolbook product for a sample of database rows against all 992
+    columns and 8 limbs, and the fold of those rows.  Uniform random residues stand in for the
+    operands (the oracle's arithmetic does not depend on their values).  Returns
+    (comparisons/s extrapolated to the whole workload, threads, sample description, seconds)."""
+    import numpy as np
+    import oracle as O
+
+    P = O.Params(**O.PAPER)
+    q = P.q
+    rng = np.random.default_rng(seed)
+    n_cols = N_EYES * P.rho
+    M_total = P.ndb + N_DB
+    ct = np.stack([rng.integers(0, q[l], size=(n_cols, P.K), dtype=np.uint64) for l in range(P.n_limbs_q)])
+    t0 = time.perf_counter()
+    Bq = O.query_extend(P, ct)
+    t_ext = time.perf_counter() - t0
+
+    def rows(S):
+        return np.stack([rng.integers(0, q[l], size=(S, P.K), dtype=np.uint64) for l in range(P.n_limbs)])
+
+    # calibrate the row count
+    S = 4
+    A = rows(S)
+    t0 = time.perf_counter()
+    O.ppmm(q, A, Bq)
+    t4 = time.perf_counter() - t0
+    S = max(4, min(4096, int(S * max(seconds_target - t_ext, 1.0) / max(t4, 1e-3))))
+    A = rows(S)
+    t0 = time.perf_counter()
+    C = O.ppmm(q, A, Bq)
+    t_mm = time.perf_counter() - t0
+    # fold of the sampled rows (a-part coefficients 30..S-1 have every source present)
+    ids = np.arange(S, dtype=np.int64)
+    t0 = time.perf_counter()
+    O.fold(P, C, ids, N_EYES, 0)
+    t_fold = time.perf_counter() - t0
+    t_full = t_ext + (t_mm + t_fold) * M_total / S
+    value = N_EYES * N_DB / t_full
+    sample = (f"oracle basis extension of the full query ({n_cols} cols x {P.K} x 2 limbs) + u128 schoolbook "
+              f"PPMM of {S} of {M_total} database rows x {n_cols} cols x 8 limbs + fold of those rows, "
+              f"extrapolated linearly in rows; uniform random residues")
+    return value, O.threads(), sample, t_ext + t_mm + t_fold
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return 0
+    times, vals = [], []
+    threads, sample = None, None
+    for i in range(args.warmup + args.steps):
+        v, threads, sample, secs = oracle_sample(seconds_target=6.0, seed=i)
+        if i >= args.warmup:
+            vals.append(v)
+            times.append(secs)
+    value = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": N_EYES * N_DB / value * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "form": "oracle u128 schoolbook (CPU)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------ GPU arm
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="icm", choices=["icm", "reference"])
+    ap.add_argument("--form", default="i8_crt", choices=["u64", "i8_digits", "i8_crt", "f16_crt"])
+    ap.add_argument("--compare-forms", default="u64,i8_digits",
+                    help="comma list of other forms timed once each on the same workload ('' to skip)")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = _dist()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2601_17561_gb300 import build as B
+    B.build()
+    from paper_2601_17561_gb300 import engine as E
+    from paper_2601_17561_gb300 import icm as C
+    from paper_2601_17561_gb300 import synth
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- setup (untimed): resident encrypted database shard and the query ciphertext
+    W = synth.make_workload(n_eyes=N_EYES, n_db=N_DB, seed=2 + 1000 * rank, planted_frac=0.05)
+    Wq = synth.make_workload(n_eyes=N_EYES, n_db=0, seed=2) if rank else W
+    eng = E.Engine(**E.PAPER).keygen()
+    db = eng.encrypt_db(W.db_codes, W.db_masks, chunk_id=rank)
+    ct = eng.encrypt_query(Wq.q_codes, Wq.q_masks, Wq.eye_ids)
+    torch.cuda.synchronize()
+    st = torch.cuda.Stream(device=dev)
+    comps = N_EYES * N_DB
+
+    def timed_form(form: str, steps: int, warmup: int):
+        """warmup (>= 1) untimed steps, barrier, then `steps` steps timed with CUDA events on the
+        launching stream; also the per-launch time of the CCMM kernel."""
+        f = C.FORMS[form]
+        op = E._u8(C.icm_query_op_bytes(eng.ctx, N_EYES, f), dev)
+        sc = E._u8(eng.scores_bytes(db, N_EYES, False), dev)
+        fo = E._u8(eng.scores_bytes(db, N_EYES, True), dev)
+        evs = []
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(st):
+            for i in range(warmup + steps):
+                if i == warmup:
+                    st.synchronize()
+                    barrier()
+                    t_start.record(st)
+                e1, e2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                q = eng.prepare(ct, N_EYES, f, stream=st, out=op)
+                e1.record(st)
+                s = eng.match(db, q, stream=st, out=sc)
+                e2.record(st)
+                eng.fold(s, stream=st, out=fo)
+                if i >= warmup:
+                    evs.append((e1, e2))
+            t_end.record(st)
+        st.synchronize()
+        total_ms = t_start.elapsed_time(t_end)
+        gemm_ms = [a.elapsed_time(b) for a, b in evs]
+        del op, sc, fo
+        return total_ms, gemm_ms
+
+    # ---- headline: K timed steps of the chosen form
+    clocks = Clocks(local)
+    total_ms, gemm_ms = timed_form(args.form, args.steps, max(args.warmup, 1))
+    clk = clocks.stop()
+    barrier()
+    t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_per_step = t.item() / args.steps
+    value = ws * comps / (ms_per_step / 1e3)
+
+    # ---- roofline of the dominant kernel (the CCMM product)
+    M, K, L, n_cols = db.m_rows, eng.K, eng.L, N_EYES * 31
+    gemm_avg_s = statistics.mean(gemm_ms) / 1e3
+    peaks = measured_peaks()
+    f = C.FORMS[args.form]
+    if args.form == "u64":
+        ops = 9.0 * M * n_cols * K * L                     # IMAD.WIDE per launch (3 x 3 20-bit limb products)
+        sm_max = peaks.get("sm_max_mhz", 2070.0)
+        peak = 152 * 32 * sm_max * 1e6                      # 152 SMs x 32 IMAD.WIDE/clk x max SM clock
+        roof = {"bound": "alu", "achieved": ops / gemm_avg_s / 1e9, "peak": peak / 1e9, "unit": "Gop/s",
+                "peak_source": "derived: 152 SMs x 32 IMAD.WIDE per clock x max SM clock"}
+    elif args.form in ("i8_digits", "i8_crt"):
+        kp = (K + 31) // 32 * 32
+        pairs = 64 if args.form == "i8_digits" else \
+            int((C.icm_query_op_bytes(eng.ctx, 1, f) - L * 31 * K * 8) // (L * 31 * kp))
+        ops = 2.0 * pairs * M * n_cols * kp * L
+        peak = 2.0 * C.icm_probe_peak(1)
+        roof = {"bound": "tensor", "achieved": ops / gemm_avg_s / 1e12, "peak": peak / 1e12, "unit": "TOP/s",
+                "peak_source": "measured in this run: int8 mma.sync.m16n8k32 issue-bound probe (no tcgen05 int8 on sm_103a)"}
+    else:
+        ops = 0.0
+        peak = peaks.get("bf16_tflops", 1900.0) * 1e12
+        roof = {"bound": "tensor", "achieved": 0.0, "peak": peak / 1e12, "unit": "TFLOP/s", "peak_source": "measured bf16"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = NCU_TRAFFIC.get(args.form)
+    roof["kernel"] = {"u64": "k_ppmm_u64", "i8_digits": "k_ppmm_i8<0>", "i8_crt": "k_ppmm_i8<1>"}.get(args.form)
+    roof["ms_per_launch"] = gemm_avg_s * 1e3
+
+    # ---- other forms, one timed step each on the same workload
+    forms = {args.form: {"value": value, "ms_per_step": ms_per_step}}
+    for other in [x for x in args.compare_forms.split(",") if x and x != args.form]:
+        tot, gm = timed_form(other, 1, 1)
+        forms[other] = {"value": comps / (tot / 1e3), "ms_per_step": tot}
+
+    # ---- end to end through the C ABI with host buffers
+    f = C.FORMS[args.form]
+    ct_bytes = C.icm_query_ct_bytes(eng.ctx, N_EYES)
+    fo_bytes = eng.scores_bytes(db, N_EYES, True)
+    h_ct = torch.empty(ct_bytes, dtype=torch.uint8, pin_memory=True)
+    h_ct.copy_(ct[:ct_bytes].cpu())
+    h_fo = torch.empty(fo_bytes, dtype=torch.uint8, pin_memory=True)
+    wsb = C.icm_match_host_workspace_bytes(eng.ctx, db.handle, N_EYES, f)
+    wsbuf = E._u8(wsb, dev)
+    with torch.cuda.stream(st):
+        C.icm_match_host(eng.ctx, db.handle, h_ct, N_EYES, f, h_fo, wsbuf, wsb, stream=st)
+        st.synchronize()
+        barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        for _ in range(args.e2e_steps):
+            C.icm_match_host(eng.ctx, db.handle, h_ct, N_EYES, f, h_fo, wsbuf, wsb, stream=st)
+        b.record(st)
+        st.synchronize()
+    e2e_ms = a.elapsed_time(b) / args.e2e_steps
+    te = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+    if ws > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e = {"value": ws * comps / (te.item() / 1e3), "unit": UNIT, "h2d_bytes_per_step": ct_bytes,
+           "d2h_bytes_per_step": fo_bytes, "ms_per_step": te.item()}
+    del wsbuf
+
+    launches_per_step = 1 + (1 if args.form != "u64" else 0) + 1 + 1
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": max(args.warmup, 1), "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.form], "data": "synthetic",
+            "config": {"workload": WORKLOAD, "form": args.form, "database_gb": round(db.buf.numel() / 1e9, 1),
+                       "l2": "inputs larger than L2 (206 GB resident database), no flush",
+                       "parallelism": "replicas" if ws == 1 else f"weak: {ws} database shards, same query"},
+            "roofline": roof, "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clk,
+            "forms": forms}
+
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        v, thr, sample, _ = oracle_sample(seconds_target=15.0)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": sample}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,221 @@
+/*
+ * icm.h -- C ABI of the GB300-native encrypted 1:N iris matching library (libicm.so).
+ *
+ * The library computes the data-parallel core of CKKS-encrypted iris matching from
+ * arxiv 2601.17561 ("Private Iris Recognition with High-Performance FHE"): encryption of an
+ * iris database in MSRLWE-RGSW form and of query eyes in MSRLWE form, the ciphertext x
+ * ciphertext matrix product (CCMM) as modular matrix products over the RNS limbs, the
+ * linear (key-free) fold of Algorithm 2, and decryption for checking.
+ *
+ * Conventions shared by every call
+ *  - Pointers named dev_* are CUDA device pointers owned by the caller; host_* / plain pointers
+ *    are host memory owned by the caller.  Sizes are in bytes unless named n_* (counts).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Calls that
+ *    take a stream only enqueue work: they return ICM_OK once the work is enqueued, and the
+ *    caller synchronises the stream (or calls icm_sync) before reading results.
+ *  - Every call returns an icm_status.  On error, out-parameters are left untouched, nothing is
+ *    allocated and no work is enqueued; icm_last_error() gives a one-line reason (per thread).
+ *    No call aborts, traps or waits without a bound.
+ *  - Handles (icm_ctx, icm_db, icm_query, icm_scores) are owned by the library until the
+ *    matching *_destroy call.  icm_db / icm_query / icm_scores only describe caller-owned device
+ *    buffers; destroying a handle never frees caller memory.  A context must outlive the
+ *    handles made from it.  Handles are immutable after creation and may be shared across
+ *    streams; icm_ctx_create/icm_keygen are not thread-safe on the same context.
+ *
+ * Data layouts (u64 residues are canonical, in [0, q_l))
+ *  - Templates: `code_bits / 8` bytes per code and per mask, bit b at byte b/8, bit b%8.
+ *  - Database chunk: [L][M][K] u64, K = d2 + N_q, M = N_db + (stored b-rows).  Row order: the
+ *    N_db a-part rows, then the b-rows of every full block, then for a partial last block its
+ *    real rows followed by the wrap-around tail coefficients [max(n_t, N_db - rho + 1), N_db)
+ *    (encryptions of zero that the fold's negacyclic shift reads).
+ *  - Query ciphertext (wire format, modulo Q): [L_q][d3][K] u64, d3 = n_eyes * rho, column
+ *    j = eye * rho + rotation holds b (d2 values) then a (N_q values).
+ *  - Scores: [L][n_cols][M] u64 (column-major: one result column contiguous, same row order as
+ *    the database chunk).  Folded scores: n_cols = n_eyes * ceil(rho / fold_k).
+ */
+#ifndef ICM_H
+#define ICM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ICM_OK = 0,
+    ICM_EINVAL = 1,        /* bad argument, size or layout                                     */
+    ICM_ENOMEM = 2,        /* host allocation failed, or caller buffer too small              */
+    ICM_ECUDA = 3,         /* a CUDA runtime call failed                                      */
+    ICM_ETIMEOUT = 4,      /* a bounded wait (host or device) ran out                          */
+    ICM_EBOUND = 5,        /* a noise, decoding or accumulator-overflow inequality fails      */
+    ICM_EUNSUPPORTED = 6   /* valid request that this build does not implement                */
+} icm_status;
+
+/* Arithmetic form of the modular matrix products (Section 6.2.2 reduces them to int8 GEMMs;
+ * on sm_103a the forms below are the exact variants this library implements). */
+typedef enum {
+    ICM_FORM_U64 = 0,        /* u64 residues on CUDA cores, exact 160-bit lazy accumulation   */
+    ICM_FORM_I8_DIGITS = 1,  /* 8 signed balanced base-256 digits per residue, int8 tensor-core
+                                products per digit pair, int32 accumulation, fused recombination */
+    ICM_FORM_I8_CRT = 2,     /* residues split over small pairwise-coprime moduli (<= 256),
+                                int8 tensor-core product per modulus, exact CRT back mod q_l  */
+    ICM_FORM_F16_CRT = 3     /* small-modulus residues as exact fp16 integers on tcgen05 tensor
+                                cores with fp32 TMEM accumulation flushed before 2^24          */
+} icm_form;
+
+typedef struct icm_ctx icm_ctx;
+typedef struct icm_db icm_db;
+typedef struct icm_query icm_query;
+typedef struct icm_scores icm_scores;
+
+/* Parameters (Section 2.3 CCMM shapes; Section 6.2.1 ring degrees N_db = 2^14, N_q = 2^13 and
+ * d = 2^14; Table 3 (computing parameters) secret Hamming weight h = 512). */
+typedef struct {
+    uint32_t log_n_db;        /* ring degree of the database encryption, N_db = 2^log_n_db     */
+    uint32_t log_n_q;         /* ring degree of the query encryption,   N_q  = 2^log_n_q       */
+    uint32_t n_limbs;         /* L: RNS primes of the database modulus Q_db = q_0 ... q_{L-1}   */
+    uint32_t n_limbs_q;       /* L_q: the first L_q primes form the query modulus Q (1 or 2)   */
+    uint32_t prime_bits;      /* every prime is below 2^prime_bits (30..60)                     */
+    uint32_t code_bits;       /* iris code length, 12800 (16 x 200 x 4 layout)                 */
+    uint32_t d2;              /* padded code length, a multiple of N_q                         */
+    uint32_t rho;             /* rotations per eye (odd), shifts -(rho-1)/2 .. (rho-1)/2        */
+    uint32_t fold_k;          /* fold group size k of Algorithm 2                               */
+    uint32_t hamming_weight;  /* h: non-zeros of every sparse ternary secret                    */
+    uint32_t log2_delta;      /* query scaling factor Delta = 2^log2_delta                     */
+    uint32_t noise_eta;       /* centred-binomial noise parameter (sigma^2 = eta / 2)           */
+    uint64_t seed;            /* master seed of every random stream                            */
+} icm_params;
+
+/* One-line description of a status code (static storage). */
+const char *icm_status_str(icm_status s);
+/* Reason for the last error returned on the calling thread ("" if none). */
+const char *icm_last_error(void);
+
+/* Create a context: validates the parameters, picks the RNS primes (the n_limbs largest
+ * primes below 2^prime_bits that are 1 mod 2^17, decreasing), and checks the noise and exact
+ * decoding inequalities of the CCMM result (ICM_EBOUND if they fail).  No device work. */
+icm_status icm_ctx_create(const icm_params *p, icm_ctx **out);
+void icm_ctx_destroy(icm_ctx *ctx);
+/* Copy the primes (n >= n_limbs values) to host memory. */
+icm_status icm_ctx_primes(const icm_ctx *ctx, uint64_t *primes, size_t n);
+
+/* Key generation (Section 2.2.2 refers to the CKKS paper): samples the database secrets
+ * s_{db,t} (degree N_db) and query secrets s_{q,t} (degree N_q) as sparse ternary polynomials
+ * with exactly h non-zeros from the context seed, and uploads their supports to the current
+ * device.  Secrets never leave the library. */
+icm_status icm_keygen(icm_ctx *ctx);
+
+/* ---------------------------------------------------------------- database (setup) ---- */
+
+/* Bytes of device memory for a database chunk of n_db templates, and its stored row count M. */
+icm_status icm_db_bytes(const icm_ctx *ctx, size_t n_db, size_t *bytes, size_t *m_rows);
+
+/* Encrypt one database chunk (Section 6.2.1: MSRLWE-RGSW pair of encryptions of M_db and of
+ * M_db * S_q, modulus Q_db = Q * Q', gadget factor Q').  codes/masks: host, n_db templates.
+ * chunk_id selects the chunk's own a-part stream.  dev_buf: caller device memory of at least
+ * icm_db_bytes bytes, which must stay alive while the handle is used. */
+icm_status icm_db_encrypt(icm_ctx *ctx, const uint8_t *codes, const uint8_t *masks, size_t n_db,
+                          uint64_t chunk_id, void *dev_buf, size_t bytes, void *stream, icm_db **out);
+void icm_db_destroy(icm_db *db);
+
+/* ---------------------------------------------------------------- query ---- */
+
+/* Bytes of the query ciphertext modulo Q (wire format) for n_eyes eyes. */
+icm_status icm_query_ct_bytes(const icm_ctx *ctx, size_t n_eyes, size_t *bytes);
+
+/* Encrypt query eyes (Section 3.1: rho rotated codes per eye; Section 2.1.3 masked bit-vector;
+ * MSRLWE under S_q modulo Q with scaling Delta).  codes/masks: host, n_eyes templates;
+ * eye_ids: host, one id per eye keying that eye's encryption randomness (an eye encrypted
+ * alone or inside a batch gives the same ciphertext columns).  dev_ct: wire format. */
+icm_status icm_query_encrypt(icm_ctx *ctx, const uint8_t *codes, const uint8_t *masks,
+                             const uint64_t *eye_ids, size_t n_eyes, void *dev_ct, size_t bytes,
+                             void *stream);
+
+/* Bytes of the prepared query operand of a form. */
+icm_status icm_query_op_bytes(const icm_ctx *ctx, size_t n_eyes, icm_form form, size_t *bytes);
+
+/* Prepare the query operand (first step of CCMM, Section 2.3): lift the ciphertext modulo Q to
+ * its centred representative and reduce it modulo every q_l (basis extension), then lay it out
+ * for `form` (digit planes or small-modulus residue planes for the tensor-core forms).
+ * dev_ct: wire format (device); dev_op: icm_query_op_bytes bytes. */
+icm_status icm_query_prepare(icm_ctx *ctx, const void *dev_ct, size_t n_eyes, icm_form form,
+                             void *dev_op, size_t bytes, void *stream, icm_query **out);
+void icm_query_destroy(icm_query *q);
+
+/* ---------------------------------------------------------------- CCMM / fold ---- */
+
+/* Bytes of the encrypted scores of one chunk for n_eyes eyes (folded != 0: after the fold). */
+icm_status icm_scores_bytes(const icm_ctx *ctx, const icm_db *db, size_t n_eyes, int folded, size_t *bytes);
+
+/* CCMM (Section 2.3): C = [A1 A2; B1 B2] * [B_q; A_q] per limb, i.e. the four plaintext modular
+ * products fused into one [M x K] x [K x d3] product per RNS limb, in the query's form.  Output
+ * bit-identical across forms.  dev_out: icm_scores_bytes(folded = 0). */
+icm_status icm_match(icm_ctx *ctx, const icm_db *db, const icm_query *q, void *dev_out, size_t bytes,
+                     void *stream, icm_scores **out);
+
+/* Fold (Algorithm 2, linear key-free part): for eye e and group g of fold_k rotations,
+ * ct'_{e,g} = sum_{r in g} X^r * ct_{e,r} on the a-part and every b-block polynomial; the shift
+ * is the global rotation index r and X^r is the negacyclic monomial shift (keyed slot rotation
+ * and the folding polynomial f are outside this library).  Tail rows of a partial block are
+ * written as zero.  dev_out: icm_scores_bytes(folded = 1). */
+icm_status icm_fold(icm_ctx *ctx, const icm_scores *in, void *dev_out, size_t bytes, void *stream,
+                    icm_scores **out);
+void icm_scores_destroy(icm_scores *s);
+
+/* Shape of a scores buffer: limbs, columns, rows. */
+icm_status icm_scores_shape(const icm_scores *s, size_t *n_limbs, size_t *n_cols, size_t *m_rows);
+
+/* Decrypt for checking only (Section 2.2.2 Dec = a*sk + b, then rounding by Q' * Delta): for
+ * every column and every real database row, the integer numerator <c'_db, c'_q> (unfolded
+ * scores) or the folded sum of numerators.  dev_num: int64 [n_cols][n_db].  Threshold
+ * decryption is outside this library. */
+icm_status icm_decrypt_scores(icm_ctx *ctx, const icm_scores *s, int64_t *dev_num, size_t n, void *stream);
+
+/* ---------------------------------------------------------------- host-buffer pipeline ---- */
+
+/* Device workspace bytes of icm_match_host for n_eyes eyes of one chunk in a form. */
+icm_status icm_match_host_workspace_bytes(const icm_ctx *ctx, const icm_db *db, size_t n_eyes, icm_form form,
+                                          size_t *bytes);
+
+/* One whole matching pass from host memory to host memory, enqueued on `stream`: copy the query
+ * ciphertext (wire format, host_ct, icm_query_ct_bytes bytes) to the device, prepare it (basis
+ * extension and planes of `form`), CCMM against `db` (Section 2.3), fold (Algorithm 2), and copy
+ * the folded scores ([L][n_eyes * ceil(rho / fold_k)][M] u64) to host_folded.  Host buffers should
+ * be page-locked for asynchronous copies; they must stay valid until the stream reaches the end
+ * of this work.  dev_ws: icm_match_host_workspace_bytes bytes of caller device memory. */
+icm_status icm_match_host(icm_ctx *ctx, const icm_db *db, const uint64_t *host_ct, size_t n_eyes, icm_form form,
+                          uint64_t *host_folded, void *dev_ws, size_t ws_bytes, void *stream);
+
+/* ---------------------------------------------------------------- plain modular product ---- */
+
+/* Workspace bytes that icm_ppmm needs for a form (0 for ICM_FORM_U64). */
+icm_status icm_ppmm_workspace_bytes(icm_form form, uint32_t n_limbs, size_t M, size_t N, size_t K, size_t *bytes);
+
+/* Plaintext modular matrix product (PPMM, Section 2.3) on arbitrary operands:
+ * dev_C[l][j][i] = sum_k dev_A[l][i][k] * dev_B[l][j][k] mod q_l, for canonical residues of
+ * primes q_l < 2^60 (host array).  A: [L][M][K], B: [L][N][K], C: [L][N][M] (u64, device). */
+icm_status icm_ppmm(icm_form form, const uint64_t *q, uint32_t n_limbs, const uint64_t *dev_A,
+                    const uint64_t *dev_B, uint64_t *dev_C, size_t M, size_t N, size_t K,
+                    void *dev_ws, size_t ws_bytes, void *stream);
+
+/* ---------------------------------------------------------------- measurement ---- */
+
+/* Peak-rate probe used as a roofline denominator (no counterpart in the paper): runs an
+ * issue-bound register-only loop of one instruction class on the current device, timed with
+ * CUDA events on `stream` (synchronises it), and returns the rate.  kind 0: IMAD.WIDE operations
+ * per second; kind 1: int8 mma.sync multiply-accumulates per second; kind 2: fp16 mma.sync
+ * multiply-accumulates per second. */
+icm_status icm_probe_peak(int kind, double *ops_per_s, void *stream);
+
+/* ---------------------------------------------------------------- synchronisation ---- */
+
+/* Wait for `stream` with a bound; ICM_ETIMEOUT if it has not finished in timeout_ms. */
+icm_status icm_sync(void *stream, uint32_t timeout_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ICM_H */

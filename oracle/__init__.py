@@ -383,14 +383,15 @@ def ppmm(q, A: np.ndarray, B: np.ndarray) -> np.ndarray:
     return C
 
 
-def fold(P: Params, C: np.ndarray, row_ids: np.ndarray, n_eyes: int) -> np.ndarray:
+def fold(P: Params, C: np.ndarray, row_ids: np.ndarray, n_eyes: int, n_real: int) -> np.ndarray:
     """Linear, key-free part of the fold of Algorithm 2: for eye e and group g of k = fold_k
     consecutive rotations, ct'_{e,g} = sum_{r in g} X^r * ct_{e,r}, on the a-part polynomial and
     on every b-block polynomial (reading: the shift is the global rotation index r; the keyed
     slot rotation Rot is replaced by the negacyclic monomial shift, and f is not applied).
     (X^r p)[i] = p[i-r] for i >= r and -p[N+i-r] for i < r.  C: [L][n_eyes*rho][M] in the chunk's
-    row layout; output [L][n_eyes*G][M] in the same layout; tail rows of a partial block are not
-    produced (zero)."""
+    row layout; output [L][n_eyes*G][M] in the same layout.  Reading for padded blocks: the tail
+    coefficients of a partial block (logical b-rows >= n_real, padding entries with no template)
+    are inputs of the wrap-around only and are not produced (zero)."""
     L, ncol, M = C.shape
     N = P.ndb
     groups = [list(range(g, min(g + P.fold_k, P.rho))) for g in range(0, P.rho, P.fold_k)]
@@ -399,6 +400,8 @@ def fold(P: Params, C: np.ndarray, row_ids: np.ndarray, n_eyes: int) -> np.ndarr
     q = P.q
     for x, rid in enumerate(row_ids):
         rid = int(rid)
+        if rid >= N + n_real:
+            continue  # tail coefficient of a partial block: not produced
         blk_base = 0 if rid < N else N + ((rid - N) // N) * N
         i = rid - blk_base
         srcs = []
@@ -413,7 +416,7 @@ def fold(P: Params, C: np.ndarray, row_ids: np.ndarray, n_eyes: int) -> np.ndarr
                 break
             srcs.append((pos[src], sgn))
         if not ok:
-            continue  # tail coefficient of a partial block: not produced
+            continue  # a source row outside the given row set (partial row sets only)
         for l in range(L):
             ql = int(q[l])
             for e in range(n_eyes):

@@ -1,0 +1,154 @@
+// Fold (Algorithm 2, linear key-free part) and decryption for checking.
+//
+// Fold: for eye e and group g of fold_k consecutive rotations, ct'_{e,g} = sum_{r in g} X^r ct_{e,r},
+// applied to the a-part polynomial and to every b-block polynomial of the MSRLWE result.  The
+// shift is the global rotation index r (Algorithm 2 rotates term rk + r' by rk + r'); X^r is the
+// negacyclic monomial shift, (X^r p)[i] = p[i - r] for i >= r and -p[N + i - r] for i < r.  Slot i
+// of the shifted result then carries database entry i - r, so that a group never stacks two
+// scores of the same database entry (Section 4.3).  The kernel is HBM-bound: every input column
+// is read once, one output column is written per group.
+//
+// Decryption (Section 2.2.2, Dec(a, b) = a * sk + b per b-block): D = C_b + s_{db,t} * C_a modulo
+// every q_l, then a fixed-point CRT gives D / Q_db modulo 1, and the numerator is the nearest
+// integer to D_centred / (Q' Delta).
+#include "icm_internal.h"
+
+namespace {
+
+using icm::LayoutDev;
+
+// Stored row position of coefficient `coef` of block `blk` (blk = -1: the a-part), or -1 if the
+// coefficient is not stored (the gap between the real rows and the tail of a partial block).
+__device__ __forceinline__ int64_t pos_of(const LayoutDev &L, int blk, uint32_t coef) {
+    if (blk < 0) return coef;
+    if ((uint32_t)blk < L.n_full) return (int64_t)L.N + (int64_t)blk * L.N + coef;
+    const int64_t base = (int64_t)L.N + (int64_t)L.n_full * L.N;
+    if (coef < L.rem) return base + coef;
+    if (coef >= L.tail_lo) return base + L.rem + (coef - L.tail_lo);
+    return -1;
+}
+
+// Block and coefficient of stored row x; tail rows of a partial block report tail = true.
+__device__ __forceinline__ void coef_of(const LayoutDev &L, uint64_t x, int &blk, uint32_t &coef, bool &tail) {
+    tail = false;
+    if (x < L.N) { blk = -1; coef = (uint32_t)x; return; }
+    const uint64_t b = x - L.N;
+    const uint64_t full = (uint64_t)L.n_full * L.N;
+    if (b < full) { blk = (int)(b / L.N); coef = (uint32_t)(b % L.N); return; }
+    const uint32_t rel = (uint32_t)(b - full);
+    blk = (int)L.n_full;
+    if (rel < L.rem) { coef = rel; return; }
+    coef = L.tail_lo + (rel - L.rem);
+    tail = true;
+}
+
+struct FoldArgs {
+    LayoutDev lay;
+    uint32_t rho, k, groups, n_eyes, L;
+    uint64_t q[ICM_MAX_LIMBS], r64[ICM_MAX_LIMBS];
+    const uint64_t *in;    // [L][n_eyes*rho][M]
+    uint64_t *out;         // [L][n_eyes*groups][M]
+};
+
+// grid: (ceil(M / 256), n_eyes * groups, L).  Each thread sums at most fold_k (<= 32) terms,
+// adding q - v for the wrapped (negated) ones; fold_k * q < 2^64 keeps the sum exact.
+__global__ void __launch_bounds__(256) k_fold(FoldArgs a) {
+    const uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t oc = blockIdx.y, l = blockIdx.z;
+    if (x >= a.lay.M) return;
+    const uint32_t e = oc / a.groups, g = oc % a.groups;
+    const uint64_t q = a.q[l];
+    uint64_t *dst = a.out + ((size_t)l * a.n_eyes * a.groups + oc) * a.lay.M + x;
+    int blk; uint32_t coef; bool tail;
+    coef_of(a.lay, x, blk, coef, tail);
+    if (tail) { *dst = 0; return; }
+    const uint32_t r0 = g * a.k, r1 = min(r0 + a.k, a.rho);
+    const uint64_t *col = a.in + ((size_t)l * a.n_eyes * a.rho + (size_t)e * a.rho) * a.lay.M;
+    uint64_t acc = 0;
+#pragma unroll 4
+    for (uint32_t r = r0; r < r1; ++r) {
+        const bool wrap = coef < r;
+        const uint32_t src = wrap ? a.lay.N + coef - r : coef - r;
+        const int64_t p = pos_of(a.lay, blk, src);
+        const uint64_t v = (p >= 0) ? col[(size_t)r * a.lay.M + p] : 0;
+        acc += wrap ? (v ? q - v : 0) : v;
+    }
+    *dst = reduce64(acc, q, a.r64[l]);
+}
+
+struct DecArgs {
+    LayoutDev lay;
+    uint32_t L, h, n_cols;
+    uint64_t q[ICM_MAX_LIMBS], r64[ICM_MAX_LIMBS];
+    icm::CrtDecode crt;
+    const int32_t *sdb_pos; const int8_t *sdb_sgn;
+    const uint64_t *sc;    // [L][n_cols][M]
+    int64_t *num;          // [n_cols][n_real]
+};
+
+// grid: (ceil(n_real / 256), n_cols).  One thread per (column, real database row).
+__global__ void __launch_bounds__(256) k_decrypt(DecArgs a) {
+    const uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t j = blockIdx.y;
+    if (r >= a.lay.n_real) return;
+    const uint32_t N = a.lay.N;
+    const uint32_t t = (uint32_t)(r / N), i = (uint32_t)(r % N);
+    const int64_t pos = pos_of(a.lay, (int)t, i);
+    uint64_t fhi = 0, flo = 0;                      // sum_l y_l floor(2^128 / q_l) mod 2^128
+    for (uint32_t l = 0; l < a.L; ++l) {
+        const uint64_t q = a.q[l];
+        const uint64_t *col = a.sc + ((size_t)l * a.n_cols + j) * a.lay.M;
+        uint64_t d = col[pos];
+        for (uint32_t c = 0; c < a.h; ++c) {
+            const uint32_t p = (uint32_t)a.sdb_pos[t * a.h + c];
+            const int s = a.sdb_sgn[t * a.h + c];
+            const uint64_t term = (i >= p) ? col[i - p] : col[N + i - p];
+            const bool neg = (i >= p) ? (s < 0) : (s > 0);
+            d = neg ? sub_mod(d, term, q) : add_mod(d, term, q);
+        }
+        const uint64_t y = mulmod_shoup(d, a.crt.inv[l], a.crt.invs[l], q);
+        // y * (rhi 2^64 + rlo) mod 2^128
+        const uint64_t plo = y * a.crt.rlo[l];
+        const uint64_t phi = __umul64hi(y, a.crt.rlo[l]) + y * a.crt.rhi[l];
+        const uint64_t nlo = flo + plo;
+        fhi = fhi + phi + (nlo < flo ? 1 : 0);
+        flo = nlo;
+    }
+    // F / 2^128 is D / Q_db modulo 1; as a signed 128-bit number it is the centred value.
+    const double frac = (double)(int64_t)fhi * 0x1p-64 + (double)flo * 0x1p-128;
+    a.num[(size_t)j * a.lay.n_real + r] = (int64_t)rint(frac * a.crt.q_over_delta);
+}
+
+}  // namespace
+
+namespace icm {
+
+cudaError_t launch_fold(const icm_ctx *c, const LayoutDev &lay, const uint64_t *d_in, uint32_t n_eyes,
+                        uint64_t *d_out, cudaStream_t st) {
+    FoldArgs a{};
+    a.lay = lay; a.rho = c->p.rho; a.k = c->p.fold_k;
+    a.groups = (c->p.rho + c->p.fold_k - 1) / c->p.fold_k;
+    a.n_eyes = n_eyes; a.L = c->p.n_limbs;
+    for (uint32_t l = 0; l < a.L; ++l) { a.q[l] = c->q[l]; a.r64[l] = c->lt.r64[l]; }
+    a.in = d_in; a.out = d_out;
+    if (n_eyes == 0 || lay.M == 0) return cudaSuccess;
+    dim3 grid((unsigned)((lay.M + 255) / 256), n_eyes * a.groups, a.L);
+    k_fold<<<grid, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_decrypt(const icm_ctx *c, const LayoutDev &lay, const uint64_t *d_scores, uint32_t n_cols,
+                           int64_t *d_num, cudaStream_t st) {
+    DecArgs a{};
+    a.lay = lay; a.L = c->p.n_limbs; a.h = c->p.hamming_weight; a.n_cols = n_cols;
+    for (uint32_t l = 0; l < a.L; ++l) { a.q[l] = c->q[l]; a.r64[l] = c->lt.r64[l]; }
+    a.crt = c->crt;
+    a.sdb_pos = c->d_sdb_pos; a.sdb_sgn = c->d_sdb_sgn;
+    a.sc = d_scores; a.num = d_num;
+    if (n_cols == 0 || lay.n_real == 0) return cudaSuccess;
+    dim3 grid((unsigned)((lay.n_real + 255) / 256), n_cols);
+    k_decrypt<<<grid, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace icm

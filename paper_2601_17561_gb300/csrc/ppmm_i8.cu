@@ -1,0 +1,376 @@
+// Plaintext modular matrix product on int8 tensor cores (Section 6.2.2 reduces the modular
+// products to int8 x int8 -> int32 GEMMs).  sm_103a has no tcgen05 int8 MMA kind, so these
+// kernels issue the warp-level mma.sync.m16n8k32.s32.s8.s8.s32.  Two exact forms:
+//
+// Digit form.  The centred lift x in (-q/2, q/2] of a residue has a unique expansion in signed
+// balanced base-256 digits, x = sum_t d_t 256^t with d_t in [-128, 127]: the bytes of
+// x + 0x8080808080808080 are d_t + 128.  Then sum_k A[i][k] B[j][k] = sum_s T_s 256^s with
+// T_s = sum_{t+u=s} sum_k d^A_t[i][k] d^B_u[j][k], one int8 GEMM per digit pair (64 per limb), the
+// pairs of one shift s sharing an int32 accumulator.  Overflow invariant: a shift with p pairs
+// sums at most p * Kc products of magnitude <= 2^14 per chunk of Kc columns, and
+// p * Kc * 2^14 <= 2^31 - 1 is kept by splitting K into chunks; after every chunk the accumulator
+// is folded into the modular result R += (T mod q) (2^(8 s) mod q).
+//
+// CRT form (small-modulus RNS, as in the paper's own RNS of small moduli below 2^8): for r
+// pairwise-coprime moduli m_i <= 256 whose product M exceeds 2 K ((q-1)/2)^2 by 2^8, one int8 GEMM
+// per modulus on the centred residues of x mod m_i gives c_i = C mod m_i exactly (K (2^7)^2 < 2^31),
+// and C mod q = sum_i y_i (M/m_i mod q) - kappa (M mod q) with y_i = c_i (M/m_i)^-1 mod m_i and
+// kappa = round(sum_i y_i / m_i) (C / M lies within 2^-8 of zero, so fp32 decides kappa exactly).
+// Residues of the database operand are formed on the fly from its digits with two dp4a.
+//
+// Tiling: 128 x 64 output tile per 256-thread block (8 warps, 32 x 32 each, 2 x 4 m16n8 tiles),
+// K in slabs of 32.  Operands are converted into shared memory directly in mma fragment order
+// (one 16-byte load per A fragment, one 8-byte load per B fragment, conflict-free).  The query
+// operand comes pre-split into int8 planes [L][P][N][Kp] (Kp: K rounded up to 32, zero padded).
+#include "icm_internal.h"
+#include "ppmm_i8.h"
+
+#include <algorithm>
+#include <cmath>
+
+namespace {
+
+constexpr int BM = 128, BN = 64, BK = 32, NT = 256;
+constexpr int MT = BM / 16, NTL = BN / 8;     // m16 and n8 tiles per block
+
+struct I8Args {
+    const uint64_t *A;      // [L][M][K] canonical residues
+    const int8_t *Bp;       // [L][P][N][Kp] planes
+    uint64_t *C;            // [L][N][M]
+    uint64_t M, N, K, Kp;
+    icm::I8Consts k;
+};
+
+__device__ __forceinline__ void mma_s8(int (&c)[4], const uint4 &a, const uint2 &b) {
+    asm volatile("mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+                 : "+r"(c[0]), "+r"(c[1]), "+r"(c[2]), "+r"(c[3])
+                 : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b.x), "r"(b.y));
+}
+
+// Balanced digits of the centred lift of 4 residues (same row, 4 consecutive k): out[t] packs
+// digit t of the 4 values (k ascending in bytes 0..3).
+__device__ __forceinline__ void digits4(const uint64_t (&x)[4], uint64_t q, uint32_t (&out)[8]) {
+    uint32_t lo[4], hi[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const uint64_t v = x[e];
+        const uint64_t c = (v > (q >> 1)) ? v - q : v;            // centred lift, two's complement
+        const uint64_t y = c + 0x8080808080808080ull;               // bytes = d_t + 128
+        lo[e] = (uint32_t)y ^ 0x80808080u;
+        hi[e] = (uint32_t)(y >> 32) ^ 0x80808080u;
+    }
+    // gather byte t of the four words
+    const uint32_t a01 = __byte_perm(lo[0], lo[1], 0x5140), a23 = __byte_perm(lo[2], lo[3], 0x5140);
+    const uint32_t b01 = __byte_perm(lo[0], lo[1], 0x7362), b23 = __byte_perm(lo[2], lo[3], 0x7362);
+    const uint32_t c01 = __byte_perm(hi[0], hi[1], 0x5140), c23 = __byte_perm(hi[2], hi[3], 0x5140);
+    const uint32_t d01 = __byte_perm(hi[0], hi[1], 0x7362), d23 = __byte_perm(hi[2], hi[3], 0x7362);
+    out[0] = __byte_perm(a01, a23, 0x5410); out[1] = __byte_perm(a01, a23, 0x7632);
+    out[2] = __byte_perm(b01, b23, 0x5410); out[3] = __byte_perm(b01, b23, 0x7632);
+    out[4] = __byte_perm(c01, c23, 0x5410); out[5] = __byte_perm(c01, c23, 0x7632);
+    out[6] = __byte_perm(d01, d23, 0x5410); out[7] = __byte_perm(d01, d23, 0x7632);
+}
+
+// Centred residue (|r| <= 128) of x mod m from the 8 digits of x: x = sum_t d_t 256^t, so
+// x = sum_t d_t w_t (mod m) with centred constants w_t = 256^t mod m; two dp4a give the sum.
+__device__ __forceinline__ int residue_from_digits(uint32_t dlo, uint32_t dhi, int wlo, int whi, int m, float inv_m) {
+    int s = __dp4a((int)dlo, wlo, 0);
+    s = __dp4a((int)dhi, whi, s);
+    if (m == 256) return (int)(int8_t)(s & 0xFF);
+    int r = s - m * __float2int_rn((float)s * inv_m);
+    const int h = (m - 1) >> 1;
+    r = r > h ? r - m : (r < -h ? r + m : r);
+    return r;
+}
+
+template <int FORM>
+__global__ void __launch_bounds__(NT, 1) k_ppmm_i8(I8Args p) {
+    __shared__ __align__(16) uint32_t sA[8][MT][32][4];
+    __shared__ __align__(16) uint32_t sB[8][NTL][32][2];
+    const uint32_t l = blockIdx.z;
+    const uint64_t m0 = (uint64_t)blockIdx.x * BM, n0 = (uint64_t)blockIdx.y * BN;
+    const uint64_t M = p.M, N = p.N, K = p.K, Kp = p.Kp;
+    const uint64_t *Al = p.A + (size_t)l * M * K;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp & 3, wn = warp >> 2;
+    const uint64_t q = p.k.q[l], r64 = p.k.r64[l];
+    const int P = FORM == 0 ? 8 : (int)p.k.n_mod;
+    const int8_t *Bl = p.Bp + (size_t)l * P * N * Kp;
+
+    uint64_t R[2][4][4];                      // digit form: modular result; CRT form: sum y_i W_i mod q
+    float F[2][4][4];                         // CRT form: sum y_i / m_i
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) { R[a][b][c] = 0; F[a][b][c] = 0.f; }
+
+    const int n_pass = FORM == 0 ? 15 : (int)p.k.n_mod;
+    for (int pass = 0; pass < n_pass; ++pass) {
+        const int t_lo = FORM == 0 ? max(0, pass - 7) : 0;
+        const int t_hi = FORM == 0 ? min(7, pass) : 0;
+        const int np = t_hi - t_lo + 1;
+        // K-chunk keeping np * Kc * 2^14 <= 2^31 - 1 (digit form); the CRT form needs one chunk
+        const uint64_t kc = FORM == 0 ? (uint64_t)((2147483647u / (16384u * (uint32_t)np)) / BK * BK) : K + BK;
+        for (uint64_t c0 = 0; c0 < K; c0 += kc) {
+            int acc[2][4][4];
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) acc[a][b][c] = 0;
+            const uint64_t c1 = min(K, c0 + kc);
+            for (uint64_t k0 = c0; k0 < c1; k0 += BK) {
+                __syncthreads();
+                // ---- A: 128 rows x 32 k, four groups of 4 consecutive k per thread
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int idx = tid + e * NT, r = idx >> 3, g = idx & 7;
+                    uint64_t x[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const uint64_t k = k0 + g * 4 + j;
+                        x[j] = (m0 + r < M && k < K) ? __ldg(Al + (m0 + r) * K + k) : 0ull;
+                    }
+                    const int mt = r >> 4, rr = r & 15;
+                    const int reg = (rr >> 3) + ((g >> 2) << 1), ln = ((rr & 7) << 2) + (g & 3);
+                    if (FORM == 0) {
+                        uint32_t d[8];
+                        digits4(x, q, d);
+                        for (int t = t_lo; t <= t_hi; ++t) sA[t][mt][ln][reg] = d[t];
+                    } else {
+                        const int m = p.k.mod[pass];
+                        const int wlo = p.k.wlo[pass], whi = p.k.whi[pass];
+                        const float im = p.k.inv_m[pass];
+                        uint32_t word = 0;
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const uint64_t v = x[j];
+                            const uint64_t y = ((v > (q >> 1)) ? v - q : v) + 0x8080808080808080ull;
+                            const int res = residue_from_digits((uint32_t)y ^ 0x80808080u, (uint32_t)(y >> 32) ^ 0x80808080u,
+                                                                wlo, whi, m, im);
+                            word |= ((uint32_t)(res & 0xFF)) << (8 * j);
+                        }
+                        sA[0][mt][ln][reg] = word;
+                    }
+                }
+                // ---- B planes: 64 columns x 32 k per plane, two words per thread
+                for (int t = t_lo; t <= t_hi; ++t) {
+                    const int u = FORM == 0 ? pass - t : pass;
+                    const int8_t *Bu = Bl + (size_t)u * N * Kp;
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        const int idx = tid + e * NT, cidx = idx >> 3, g = idx & 7;
+                        uint32_t w = 0;
+                        if (n0 + cidx < N) w = __ldg(reinterpret_cast<const uint32_t *>(Bu + (n0 + cidx) * Kp + k0 + g * 4));
+                        const int nt = cidx >> 3;
+                        sB[FORM == 0 ? t : 0][nt][((cidx & 7) << 2) + (g & 3)][g >> 2] = w;
+                    }
+                }
+                __syncthreads();
+                // ---- MMA: all pairs of this pass
+                for (int t = t_lo; t <= t_hi; ++t) {
+                    const int ta = FORM == 0 ? t : 0;
+                    uint4 af[2];
+                    uint2 bf[4];
+#pragma unroll
+                    for (int a = 0; a < 2; ++a) af[a] = *reinterpret_cast<const uint4 *>(&sA[ta][wm * 2 + a][lane][0]);
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) bf[b] = *reinterpret_cast<const uint2 *>(&sB[ta][wn * 4 + b][lane][0]);
+#pragma unroll
+                    for (int a = 0; a < 2; ++a)
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) mma_s8(acc[a][b], af[a], bf[b]);
+                }
+            }
+            // ---- fold the chunk's accumulator into the modular result
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        if (FORM == 0) {
+                            const uint64_t v = reduce_s64((int64_t)acc[a][b][c], q, r64);
+                            R[a][b][c] = add_mod(R[a][b][c], mulmod_shoup(v, p.k.pw8[l][pass], p.k.pw8s[l][pass], q), q);
+                        } else {
+                            const int m = p.k.mod[pass];
+                            int ci = acc[a][b][c] % m;
+                            ci = ci < 0 ? ci + m : ci;                                        // C mod m_i
+                            const int y = (int)(((uint32_t)ci * (uint32_t)p.k.yinv[pass]) % (uint32_t)m);
+                            R[a][b][c] = add_mod(R[a][b][c], mulmod_shoup((uint64_t)y, p.k.W[l][pass], p.k.Ws[l][pass], q), q);
+                            F[a][b][c] += (float)y * p.k.inv_m[pass];
+                        }
+                    }
+        }
+    }
+    // ---- store (column-major output)
+    const int g = lane >> 2, tq = lane & 3;
+    uint64_t *Cl = p.C + (size_t)l * N * M;
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const uint64_t row = m0 + (uint64_t)(wm * 2 + a) * 16 + g + (c >> 1) * 8;
+                const uint64_t col = n0 + (uint64_t)(wn * 4 + b) * 8 + tq * 2 + (c & 1);
+                if (row >= M || col >= N) continue;
+                uint64_t v = R[a][b][c];
+                if (FORM == 1) {
+                    const uint64_t kappa = (uint64_t)__float2int_rn(F[a][b][c]);
+                    v = sub_mod(v, mulmod_shoup(kappa, p.k.Mq[l], p.k.Mqs[l], q), q);
+                }
+                Cl[col * M + row] = v;
+            }
+}
+
+// Query planes: for each residue of the extended operand [L][N][K], digit planes (8) or
+// centred residue planes (n_mod) in [L][P][N][Kp], zero padded to Kp.
+template <int FORM>
+__global__ void __launch_bounds__(256) k_planes(const uint64_t *op, int8_t *planes, uint64_t N, uint64_t K,
+                                                uint64_t Kp, icm::I8Consts k) {
+    const uint32_t l = blockIdx.y;
+    const int P = FORM == 0 ? 8 : (int)k.n_mod;
+    const uint64_t q = k.q[l];
+    const uint64_t total = N * Kp;
+    for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t j = idx / Kp, kk = idx % Kp;
+        const uint64_t v = kk < K ? op[((size_t)l * N + j) * K + kk] : 0;
+        const uint64_t c = (v > (q >> 1)) ? v - q : v;
+        const uint64_t y = c + 0x8080808080808080ull;
+        int8_t *dst = planes + (size_t)l * P * N * Kp + idx;
+        if (FORM == 0) {
+#pragma unroll
+            for (int t = 0; t < 8; ++t) dst[(size_t)t * N * Kp] = (int8_t)(((y >> (8 * t)) & 0xFF) ^ 0x80);
+        } else {
+            const uint32_t dlo = (uint32_t)y ^ 0x80808080u, dhi = (uint32_t)(y >> 32) ^ 0x80808080u;
+            for (int i = 0; i < P; ++i)
+                dst[(size_t)i * N * Kp] = (int8_t)residue_from_digits(dlo, dhi, k.wlo[i], k.whi[i], k.mod[i], k.inv_m[i]);
+        }
+    }
+}
+
+}  // namespace
+
+namespace icm {
+
+cudaError_t launch_planes(int form, const I8Consts &k, const uint64_t *op, int8_t *planes, uint64_t N, uint64_t K,
+                          uint64_t Kp, cudaStream_t st) {
+    if (N == 0 || Kp == 0) return cudaSuccess;
+    const uint64_t total = N * Kp;
+    const unsigned blocks = (unsigned)std::min<uint64_t>((total + 255) / 256, 152u * 32u);
+    dim3 grid(blocks, k.n_limbs);
+    if (form == ICM_FORM_I8_DIGITS) k_planes<0><<<grid, 256, 0, st>>>(op, planes, N, K, Kp, k);
+    else k_planes<1><<<grid, 256, 0, st>>>(op, planes, N, K, Kp, k);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ppmm_i8(int form, const I8Consts &k, const uint64_t *A, const int8_t *Bp, uint64_t *C, uint64_t M,
+                           uint64_t N, uint64_t K, uint64_t Kp, cudaStream_t st) {
+    if (M == 0 || N == 0) return cudaSuccess;
+    I8Args a{A, Bp, C, M, N, K, Kp, k};
+    dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((N + BN - 1) / BN), k.n_limbs);
+    if (form == ICM_FORM_I8_DIGITS) k_ppmm_i8<0><<<grid, NT, 0, st>>>(a);
+    else k_ppmm_i8<1><<<grid, NT, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace icm
+
+namespace icm {
+
+namespace {
+using u128 = unsigned __int128;
+uint64_t mulmod_h(uint64_t a, uint64_t b, uint64_t q) { return (uint64_t)((u128)a * b % q); }
+uint64_t powmod_h(uint64_t b, uint64_t e, uint64_t q) {
+    uint64_t r = 1 % q;
+    b %= q;
+    while (e) { if (e & 1) r = mulmod_h(r, b, q); b = mulmod_h(b, b, q); e >>= 1; }
+    return r;
+}
+uint64_t gcd_h(uint64_t a, uint64_t b) { while (b) { uint64_t t = a % b; a = b; b = t; } return a; }
+// Inverse of a modulo m (gcd 1) by the extended Euclidean algorithm.
+int64_t inv_h(int64_t a, int64_t m) {
+    int64_t g = m, x = 0, x1 = 1, a1 = a % m;
+    while (a1) { int64_t qq = g / a1, t = g - qq * a1; g = a1; a1 = t; t = x - qq * x1; x = x1; x1 = t; }
+    return ((x % m) + m) % m;
+}
+uint64_t shoup_h(uint64_t w, uint64_t q) { return (uint64_t)(((u128)w << 64) / q); }
+
+// Greedy: the largest pairwise-coprime integers <= 256, as many as the range needs.
+std::vector<int> crt_moduli(const std::vector<uint64_t> &q, uint64_t K) {
+    uint64_t qmax = 0;
+    for (uint64_t v : q) qmax = v > qmax ? v : qmax;
+    // |C| <= K ((qmax-1)/2)^2; need log2 M >= 1 + log2|C| + 8 (kappa margin)
+    const double need = 1.0 + std::log2((double)(K ? K : 1)) + 2.0 * std::log2((double)((qmax - 1) / 2 + 1)) + 8.0;
+    std::vector<int> mods;
+    double have = 0;
+    for (int n = 256; n >= 3 && have < need && mods.size() < ICM_MAX_MODULI; --n) {
+        bool ok = true;
+        for (int m : mods) if (gcd_h((uint64_t)n, (uint64_t)m) != 1) { ok = false; break; }
+        if (ok) { mods.push_back(n); have += std::log2((double)n); }
+    }
+    if (have < need) mods.clear();
+    return mods;
+}
+}  // namespace
+
+uint32_t i8_planes(int form, const std::vector<uint64_t> &q, uint64_t K) {
+    return form == ICM_FORM_I8_DIGITS ? 8u : (uint32_t)crt_moduli(q, K).size();
+}
+
+bool make_i8_consts(int form, const std::vector<uint64_t> &q, uint64_t K, I8Consts &k, const char **why) {
+    k = I8Consts{};
+    k.n_limbs = (uint32_t)q.size();
+    for (size_t l = 0; l < q.size(); ++l) {
+        if (q[l] >= (1ull << 60)) { *why = "int8 forms need primes below 2^60 (8 balanced digits)"; return false; }
+        k.q[l] = q[l];
+        k.r64[l] = (uint64_t)(((u128)1 << 64) / q[l]);
+        for (int s = 0; s < 15; ++s) { k.pw8[l][s] = powmod_h(2, 8ull * s, q[l]); k.pw8s[l][s] = shoup_h(k.pw8[l][s], q[l]); }
+    }
+    if (form == ICM_FORM_I8_DIGITS) {
+        // chunking keeps p * Kc * 2^14 <= 2^31 - 1 for every shift (p <= 8); nothing else to check
+        k.n_mod = 0;
+        return true;
+    }
+    // CRT form: every int32 accumulator sums K products of magnitude <= 2^14
+    if (K * 16384ull > 2147483647ull) { *why = "K too deep for int32 accumulation of the CRT form (K <= 131071)"; return false; }
+    std::vector<int> mods = crt_moduli(q, K);
+    if (mods.empty()) { *why = "no set of small moduli covers the product range"; return false; }
+    k.n_mod = (uint32_t)mods.size();
+    for (size_t i = 0; i < mods.size(); ++i) {
+        const int m = mods[i];
+        int w[8];
+        for (int t = 0; t < 8; ++t) {
+            int v = (int)powmod_h(256, (uint64_t)t, (uint64_t)m);
+            if (m == 256) v = (t == 0) ? 1 : 0;
+            else if (v > (m - 1) / 2) v -= m;              // centred
+            w[t] = v;
+        }
+        k.mod[i] = m;
+        k.wlo[i] = (int32_t)((uint32_t)(uint8_t)w[0] | ((uint32_t)(uint8_t)w[1] << 8) | ((uint32_t)(uint8_t)w[2] << 16) | ((uint32_t)(uint8_t)w[3] << 24));
+        k.whi[i] = (int32_t)((uint32_t)(uint8_t)w[4] | ((uint32_t)(uint8_t)w[5] << 8) | ((uint32_t)(uint8_t)w[6] << 16) | ((uint32_t)(uint8_t)w[7] << 24));
+        k.inv_m[i] = 1.0f / (float)m;
+        // (M / m_i) mod m_i and its inverse
+        uint64_t hat = 1;
+        for (size_t j = 0; j < mods.size(); ++j) if (j != i) hat = hat * (uint64_t)mods[j] % (uint64_t)m;
+        k.yinv[i] = (int32_t)inv_h((int64_t)hat, m);
+        for (size_t l = 0; l < q.size(); ++l) {
+            uint64_t W = 1 % q[l];
+            for (size_t j = 0; j < mods.size(); ++j) if (j != i) W = mulmod_h(W, (uint64_t)mods[j], q[l]);
+            k.W[l][i] = W;
+            k.Ws[l][i] = shoup_h(W, q[l]);
+        }
+    }
+    for (size_t l = 0; l < q.size(); ++l) {
+        uint64_t Mq = 1 % q[l];
+        for (int m : mods) Mq = mulmod_h(Mq, (uint64_t)m, q[l]);
+        k.Mq[l] = Mq;
+        k.Mqs[l] = shoup_h(Mq, q[l]);
+    }
+    return true;
+}
+
+}  // namespace icm

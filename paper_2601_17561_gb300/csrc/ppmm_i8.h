@@ -1,0 +1,38 @@
+// Constants of the int8 tensor-core forms (digit pairs and small-modulus CRT), passed to kernels
+// by value.
+#pragma once
+#include <cstdint>
+#include <vector>
+#include <cuda_runtime.h>
+#include "icm_device.cuh"
+
+#define ICM_MAX_MODULI 24
+
+namespace icm {
+
+struct I8Consts {
+    uint32_t n_limbs, n_mod;
+    uint64_t q[ICM_MAX_LIMBS], r64[ICM_MAX_LIMBS];
+    // digit form: 2^(8 s) mod q_l for shifts s = 0..14, with Shoup companions
+    uint64_t pw8[ICM_MAX_LIMBS][15], pw8s[ICM_MAX_LIMBS][15];
+    // CRT form: moduli, packed centred constants 256^t mod m (t = 0..3 and 4..7), 1/m,
+    // (M/m_i)^-1 mod m_i, (M/m_i) mod q_l and M mod q_l with Shoup companions
+    int32_t mod[ICM_MAX_MODULI], wlo[ICM_MAX_MODULI], whi[ICM_MAX_MODULI], yinv[ICM_MAX_MODULI];
+    float inv_m[ICM_MAX_MODULI];
+    uint64_t W[ICM_MAX_LIMBS][ICM_MAX_MODULI], Ws[ICM_MAX_LIMBS][ICM_MAX_MODULI];
+    uint64_t Mq[ICM_MAX_LIMBS], Mqs[ICM_MAX_LIMBS];
+};
+
+// Builds the constants for primes q and contraction depth K; returns false (with a reason in
+// `why`) if the int32 overflow invariant or the CRT range cannot be met.
+bool make_i8_consts(int form, const std::vector<uint64_t> &q, uint64_t K, I8Consts &out, const char **why);
+// Planes per residue: 8 digit planes or n_mod residue planes.
+uint32_t i8_planes(int form, const std::vector<uint64_t> &q, uint64_t K);
+inline uint64_t i8_kpad(uint64_t K) { return (K + 31) / 32 * 32; }
+
+cudaError_t launch_planes(int form, const I8Consts &k, const uint64_t *op, int8_t *planes, uint64_t N, uint64_t K,
+                          uint64_t Kp, cudaStream_t st);
+cudaError_t launch_ppmm_i8(int form, const I8Consts &k, const uint64_t *A, const int8_t *Bp, uint64_t *C, uint64_t M,
+                           uint64_t N, uint64_t K, uint64_t Kp, cudaStream_t st);
+
+}  // namespace icm

@@ -1,0 +1,161 @@
+"""Convenience layer over the C ABI: PyTorch device buffers sized by the library and handles that
+keep them alive.  Every computation is a libicm call; this module only allocates and marshals."""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+import torch
+
+from . import icm as C
+
+# Named parameter sets.  TINY: ring degree 2^12, three primes below 2^50, Delta = 2^26.
+# PAPER: N_db = 2^14, N_q = 2^13, d = 2^14 (Section 6.2.1), eight primes below 2^60.
+TINY = dict(log_n_db=12, log_n_q=12, n_limbs=3, n_limbs_q=1, prime_bits=50, log2_delta=26, seed=1)
+PAPER = dict(log_n_db=14, log_n_q=13, n_limbs=8, n_limbs_q=2, prime_bits=60, log2_delta=60, seed=2)
+
+
+def _u8(nbytes: int, device) -> torch.Tensor:
+    # 256-byte alignment comes from the caching allocator; round the size up to 16 bytes
+    return torch.empty(max(16, (nbytes + 15) // 16 * 16), dtype=torch.uint8, device=device)
+
+
+@dataclasses.dataclass
+class Db:
+    handle: object
+    buf: torch.Tensor
+    n_real: int
+    m_rows: int
+    chunk_id: int
+
+    def __del__(self):
+        if self.handle is not None:
+            C.icm_db_destroy(self.handle)
+            self.handle = None
+
+
+@dataclasses.dataclass
+class Query:
+    handle: object
+    buf: torch.Tensor
+    n_eyes: int
+    form: int
+
+    def __del__(self):
+        if self.handle is not None:
+            C.icm_query_destroy(self.handle)
+            self.handle = None
+
+
+@dataclasses.dataclass
+class Scores:
+    handle: object
+    buf: torch.Tensor
+    shape: tuple          # (L, n_cols, M)
+    n_eyes: int
+    folded: bool
+    db: Db
+
+    def residues(self) -> np.ndarray:
+        L, n, M = self.shape
+        return self.buf[: L * n * M * 8].view(torch.int64).cpu().numpy().view(np.uint64).reshape(L, n, M)
+
+    def __del__(self):
+        if self.handle is not None:
+            C.icm_scores_destroy(self.handle)
+            self.handle = None
+
+
+class Engine:
+    """One library context (parameters, primes, secrets) on the current CUDA device."""
+
+    def __init__(self, log_n_db, log_n_q, n_limbs, n_limbs_q, prime_bits, log2_delta, seed, rho=31, fold_k=16,
+                 hamming_weight=512, noise_eta=21, d2=1 << 14, code_bits=12800, device="cuda"):
+        self.device = torch.device(device)
+        self.params = C.icm_params(log_n_db=log_n_db, log_n_q=log_n_q, n_limbs=n_limbs, n_limbs_q=n_limbs_q,
+                                   prime_bits=prime_bits, code_bits=code_bits, d2=d2, rho=rho, fold_k=fold_k,
+                                   hamming_weight=hamming_weight, log2_delta=log2_delta, noise_eta=noise_eta,
+                                   seed=seed)
+        self.ctx = C.icm_ctx_create(self.params)
+        self.keyed = False
+        self.L = n_limbs
+        self.rho = rho
+        self.fold_k = fold_k
+        self.K = d2 + (1 << log_n_q)
+
+    def keygen(self):
+        with torch.cuda.device(self.device):
+            C.icm_keygen(self.ctx)
+        self.keyed = True
+        return self
+
+    @property
+    def primes(self):
+        return C.icm_ctx_primes(self.ctx, self.L)
+
+    def __del__(self):
+        if getattr(self, "ctx", None) is not None:
+            C.icm_ctx_destroy(self.ctx)
+            self.ctx = None
+
+    # -------------------------------------------------------------------- setup
+    def encrypt_db(self, codes: np.ndarray, masks: np.ndarray, chunk_id: int = 0, stream=None) -> Db:
+        codes = np.ascontiguousarray(codes, np.uint8)
+        masks = np.ascontiguousarray(masks, np.uint8)
+        n = codes.shape[0]
+        nbytes, m_rows = C.icm_db_bytes(self.ctx, n)
+        buf = _u8(nbytes, self.device)
+        h = C.icm_db_encrypt(self.ctx, codes, masks, n, chunk_id, buf, nbytes, stream)
+        return Db(h, buf, n, m_rows, chunk_id)
+
+    def encrypt_query(self, codes: np.ndarray, masks: np.ndarray, eye_ids, stream=None) -> torch.Tensor:
+        codes = np.ascontiguousarray(codes, np.uint8)
+        masks = np.ascontiguousarray(masks, np.uint8)
+        ids = np.ascontiguousarray(np.asarray(eye_ids, np.uint64))
+        n = codes.shape[0]
+        nbytes = C.icm_query_ct_bytes(self.ctx, n)
+        buf = _u8(nbytes, self.device)
+        C.icm_query_encrypt(self.ctx, codes, masks, ids, n, buf, nbytes, stream)
+        return buf
+
+    # -------------------------------------------------------------------- hot path
+    def prepare(self, ct: torch.Tensor, n_eyes: int, form="u64", stream=None, out: torch.Tensor = None) -> Query:
+        f = C.FORMS[form] if isinstance(form, str) else form
+        nbytes = C.icm_query_op_bytes(self.ctx, n_eyes, f)
+        buf = out if out is not None else _u8(nbytes, self.device)
+        h = C.icm_query_prepare(self.ctx, ct, n_eyes, f, buf, nbytes, stream)
+        return Query(h, buf, n_eyes, f)
+
+    def scores_bytes(self, db: Db, n_eyes: int, folded: bool) -> int:
+        return C.icm_scores_bytes(self.ctx, db.handle, n_eyes, folded)
+
+    def match(self, db: Db, q: Query, stream=None, out: torch.Tensor = None) -> Scores:
+        nbytes = C.icm_scores_bytes(self.ctx, db.handle, q.n_eyes, 0)
+        buf = out if out is not None else _u8(nbytes, self.device)
+        h = C.icm_match(self.ctx, db.handle, q.handle, buf, nbytes, stream)
+        return Scores(h, buf, C.icm_scores_shape(h), q.n_eyes, False, db)
+
+    def fold(self, s: Scores, stream=None, out: torch.Tensor = None) -> Scores:
+        nbytes = C.icm_scores_bytes(self.ctx, s.db.handle, s.n_eyes, 1)
+        buf = out if out is not None else _u8(nbytes, self.device)
+        h = C.icm_fold(self.ctx, s.handle, buf, nbytes, stream)
+        return Scores(h, buf, C.icm_scores_shape(h), s.n_eyes, True, s.db)
+
+    def decrypt(self, s: Scores, stream=None) -> torch.Tensor:
+        n = s.shape[1] * s.db.n_real
+        out = torch.empty(max(n, 1), dtype=torch.int64, device=self.device)
+        C.icm_decrypt_scores(self.ctx, s.handle, out, n, stream)
+        return out[:n].view(s.shape[1], s.db.n_real)
+
+
+def ppmm(form, q, A: torch.Tensor, B: torch.Tensor, stream=None) -> torch.Tensor:
+    """Plain modular product on device tensors (int64 views of u64 residues):
+    A [L][M][K], B [L][N][K] -> C [L][N][M]."""
+    f = C.FORMS[form] if isinstance(form, str) else form
+    L, M, K = A.shape
+    N = B.shape[1]
+    Cm = torch.empty((L, N, M), dtype=torch.int64, device=A.device)
+    ws_bytes = C.icm_ppmm_workspace_bytes(f, L, M, N, K)
+    ws = _u8(ws_bytes, A.device) if ws_bytes else None
+    C.icm_ppmm(f, q, L, A, B, Cm, M, N, K, ws, ws_bytes, stream)
+    return Cm

@@ -1,0 +1,238 @@
+"""Thin ctypes binding of libicm (include/icm.h), with the C entry points under the same names.
+
+Argument marshalling only: every step of the matching path runs in the library's CUDA kernels.
+PyTorch provides device memory (uint8 tensors sized by the *_bytes queries) and streams.  If the
+compiled library is missing, importing the binding raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libicm.so")
+
+ICM_OK, ICM_EINVAL, ICM_ENOMEM, ICM_ECUDA, ICM_ETIMEOUT, ICM_EBOUND, ICM_EUNSUPPORTED = range(7)
+ICM_FORM_U64, ICM_FORM_I8_DIGITS, ICM_FORM_I8_CRT, ICM_FORM_F16_CRT = range(4)
+FORMS = {"u64": ICM_FORM_U64, "i8_digits": ICM_FORM_I8_DIGITS, "i8_crt": ICM_FORM_I8_CRT, "f16_crt": ICM_FORM_F16_CRT}
+
+
+class IcmError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        self.status = status
+        super().__init__(f"{where}: status {status} ({detail})")
+
+
+class icm_params(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint32) for n in (
+        "log_n_db", "log_n_q", "n_limbs", "n_limbs_q", "prime_bits", "code_bits", "d2", "rho", "fold_k",
+        "hamming_weight", "log2_delta", "noise_eta")] + [("seed", ctypes.c_uint64)]
+
+
+_lib = None
+_vp, _sz, _u32, _u64, _i32 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+
+_SIGS = {
+    "icm_status_str": (ctypes.c_char_p, [_i32]),
+    "icm_last_error": (ctypes.c_char_p, []),
+    "icm_ctx_create": (_i32, [ctypes.POINTER(icm_params), ctypes.POINTER(_vp)]),
+    "icm_ctx_destroy": (None, [_vp]),
+    "icm_ctx_primes": (_i32, [_vp, _vp, _sz]),
+    "icm_keygen": (_i32, [_vp]),
+    "icm_db_bytes": (_i32, [_vp, _sz, ctypes.POINTER(_sz), ctypes.POINTER(_sz)]),
+    "icm_db_encrypt": (_i32, [_vp, _vp, _vp, _sz, _u64, _vp, _sz, _vp, ctypes.POINTER(_vp)]),
+    "icm_db_destroy": (None, [_vp]),
+    "icm_query_ct_bytes": (_i32, [_vp, _sz, ctypes.POINTER(_sz)]),
+    "icm_query_encrypt": (_i32, [_vp, _vp, _vp, _vp, _sz, _vp, _sz, _vp]),
+    "icm_query_op_bytes": (_i32, [_vp, _sz, _i32, ctypes.POINTER(_sz)]),
+    "icm_query_prepare": (_i32, [_vp, _vp, _sz, _i32, _vp, _sz, _vp, ctypes.POINTER(_vp)]),
+    "icm_query_destroy": (None, [_vp]),
+    "icm_scores_bytes": (_i32, [_vp, _vp, _sz, _i32, ctypes.POINTER(_sz)]),
+    "icm_match": (_i32, [_vp, _vp, _vp, _vp, _sz, _vp, ctypes.POINTER(_vp)]),
+    "icm_fold": (_i32, [_vp, _vp, _vp, _sz, _vp, ctypes.POINTER(_vp)]),
+    "icm_scores_destroy": (None, [_vp]),
+    "icm_scores_shape": (_i32, [_vp, ctypes.POINTER(_sz), ctypes.POINTER(_sz), ctypes.POINTER(_sz)]),
+    "icm_decrypt_scores": (_i32, [_vp, _vp, _vp, _sz, _vp]),
+    "icm_ppmm_workspace_bytes": (_i32, [_i32, _u32, _sz, _sz, _sz, ctypes.POINTER(_sz)]),
+    "icm_ppmm": (_i32, [_i32, _vp, _u32, _vp, _vp, _vp, _sz, _sz, _sz, _vp, _sz, _vp]),
+    "icm_sync": (_i32, [_vp, _u32]),
+    "icm_match_host_workspace_bytes": (_i32, [_vp, _vp, _sz, _i32, ctypes.POINTER(_sz)]),
+    "icm_match_host": (_i32, [_vp, _vp, _vp, _sz, _i32, _vp, _vp, _sz, _vp]),
+    "icm_probe_peak": (_i32, [_i32, ctypes.POINTER(ctypes.c_double), _vp]),
+}
+
+
+def lib() -> ctypes.CDLL:
+    """Load libicm.so (built by paper_2601_17561_gb300.build); raise if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libicm.so not built at {LIB_PATH}: run paper_2601_17561_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != ICM_OK:
+        detail = lib().icm_last_error().decode()
+        raise IcmError(status, where, detail or lib().icm_status_str(status).decode())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(stream)
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return ctypes.c_void_p(x.data_ptr())
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data_as(ctypes.c_void_p)
+    return ctypes.c_void_p(x)
+
+
+# ------------------------------------------------------------------ same-name wrappers
+
+def icm_status_str(s: int) -> str:
+    return lib().icm_status_str(s).decode()
+
+
+def icm_ctx_create(p: icm_params):
+    h = ctypes.c_void_p()
+    _check(lib().icm_ctx_create(ctypes.byref(p), ctypes.byref(h)), "icm_ctx_create")
+    return h
+
+
+def icm_ctx_destroy(ctx):
+    lib().icm_ctx_destroy(ctx)
+
+
+def icm_ctx_primes(ctx, n: int = 8):
+    arr = (ctypes.c_uint64 * n)()
+    _check(lib().icm_ctx_primes(ctx, arr, n), "icm_ctx_primes")
+    return list(arr)
+
+
+def icm_keygen(ctx):
+    _check(lib().icm_keygen(ctx), "icm_keygen")
+
+
+def icm_db_bytes(ctx, n_db: int):
+    b, m = ctypes.c_size_t(), ctypes.c_size_t()
+    _check(lib().icm_db_bytes(ctx, n_db, ctypes.byref(b), ctypes.byref(m)), "icm_db_bytes")
+    return b.value, m.value
+
+
+def icm_db_encrypt(ctx, codes, masks, n_db, chunk_id, dev_buf, nbytes, stream=None):
+    h = ctypes.c_void_p()
+    _check(lib().icm_db_encrypt(ctx, _ptr(codes), _ptr(masks), n_db, chunk_id, _ptr(dev_buf), nbytes,
+                                _stream(stream), ctypes.byref(h)), "icm_db_encrypt")
+    return h
+
+
+def icm_db_destroy(h):
+    lib().icm_db_destroy(h)
+
+
+def icm_query_ct_bytes(ctx, n_eyes):
+    b = ctypes.c_size_t()
+    _check(lib().icm_query_ct_bytes(ctx, n_eyes, ctypes.byref(b)), "icm_query_ct_bytes")
+    return b.value
+
+
+def icm_query_encrypt(ctx, codes, masks, eye_ids, n_eyes, dev_ct, nbytes, stream=None):
+    _check(lib().icm_query_encrypt(ctx, _ptr(codes), _ptr(masks), _ptr(eye_ids), n_eyes, _ptr(dev_ct), nbytes,
+                                   _stream(stream)), "icm_query_encrypt")
+
+
+def icm_query_op_bytes(ctx, n_eyes, form):
+    b = ctypes.c_size_t()
+    _check(lib().icm_query_op_bytes(ctx, n_eyes, form, ctypes.byref(b)), "icm_query_op_bytes")
+    return b.value
+
+
+def icm_query_prepare(ctx, dev_ct, n_eyes, form, dev_op, nbytes, stream=None):
+    h = ctypes.c_void_p()
+    _check(lib().icm_query_prepare(ctx, _ptr(dev_ct), n_eyes, form, _ptr(dev_op), nbytes, _stream(stream),
+                                   ctypes.byref(h)), "icm_query_prepare")
+    return h
+
+
+def icm_query_destroy(h):
+    lib().icm_query_destroy(h)
+
+
+def icm_scores_bytes(ctx, db, n_eyes, folded):
+    b = ctypes.c_size_t()
+    _check(lib().icm_scores_bytes(ctx, db, n_eyes, int(folded), ctypes.byref(b)), "icm_scores_bytes")
+    return b.value
+
+
+def icm_match(ctx, db, q, dev_out, nbytes, stream=None):
+    h = ctypes.c_void_p()
+    _check(lib().icm_match(ctx, db, q, _ptr(dev_out), nbytes, _stream(stream), ctypes.byref(h)), "icm_match")
+    return h
+
+
+def icm_fold(ctx, scores, dev_out, nbytes, stream=None):
+    h = ctypes.c_void_p()
+    _check(lib().icm_fold(ctx, scores, _ptr(dev_out), nbytes, _stream(stream), ctypes.byref(h)), "icm_fold")
+    return h
+
+
+def icm_scores_destroy(h):
+    lib().icm_scores_destroy(h)
+
+
+def icm_scores_shape(h):
+    a, b, c = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
+    _check(lib().icm_scores_shape(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "icm_scores_shape")
+    return a.value, b.value, c.value
+
+
+def icm_decrypt_scores(ctx, scores, dev_num, n, stream=None):
+    _check(lib().icm_decrypt_scores(ctx, scores, _ptr(dev_num), n, _stream(stream)), "icm_decrypt_scores")
+
+
+def icm_ppmm_workspace_bytes(form, n_limbs, M, N, K):
+    b = ctypes.c_size_t()
+    _check(lib().icm_ppmm_workspace_bytes(form, n_limbs, M, N, K, ctypes.byref(b)), "icm_ppmm_workspace_bytes")
+    return b.value
+
+
+def icm_ppmm(form, q, n_limbs, dev_A, dev_B, dev_C, M, N, K, dev_ws=None, ws_bytes=0, stream=None):
+    qa = (ctypes.c_uint64 * n_limbs)(*[int(x) for x in q[:n_limbs]])
+    _check(lib().icm_ppmm(form, qa, n_limbs, _ptr(dev_A), _ptr(dev_B), _ptr(dev_C), M, N, K, _ptr(dev_ws),
+                          ws_bytes, _stream(stream)), "icm_ppmm")
+
+
+def icm_match_host_workspace_bytes(ctx, db, n_eyes, form):
+    b = ctypes.c_size_t()
+    _check(lib().icm_match_host_workspace_bytes(ctx, db, n_eyes, form, ctypes.byref(b)), "icm_match_host_workspace_bytes")
+    return b.value
+
+
+def icm_match_host(ctx, db, host_ct, n_eyes, form, host_folded, dev_ws, ws_bytes, stream=None):
+    _check(lib().icm_match_host(ctx, db, _ptr(host_ct), n_eyes, form, _ptr(host_folded), _ptr(dev_ws), ws_bytes,
+                                _stream(stream)), "icm_match_host")
+
+
+def icm_probe_peak(kind: int, stream=None) -> float:
+    v = ctypes.c_double()
+    _check(lib().icm_probe_peak(kind, ctypes.byref(v), _stream(stream)), "icm_probe_peak")
+    return v.value
+
+
+def icm_sync(stream=None, timeout_ms: int = 600000):
+    _check(lib().icm_sync(_stream(stream), timeout_ms), "icm_sync")

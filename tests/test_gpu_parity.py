@@ -1,0 +1,181 @@
+"""GPU parity: every stage of the CUDA path against the oracle on the same seeded inputs.
+
+Tiny workload (ring degree 2^12, three primes below 2^50, 4 eyes x 31 rotations, 256 database
+templates): query ciphertext, extended query operand, encrypted database, CCMM residues and fold
+residues must be bit-identical to the oracle's; decrypted numerators must equal the cleartext
+inner products <c'_db, c'_q> exactly (so decoded distances equal the FP64 cleartext distances and
+match bits are identical)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2601_17561_gb300 import build as B
+from paper_2601_17561_gb300 import engine as E
+from paper_2601_17561_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _u64(t: torch.Tensor, shape):
+    n = int(np.prod(shape))
+    return t[: n * 8].view(torch.int64).cpu().numpy().view(np.uint64).reshape(shape)
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    B.build()
+    P = O.Params(**O.TINY)
+    W = synth.make_workload(**synth.TINY)
+    ids = O.db_layout(W.db_codes.shape[0], P.ndb, P.rho)
+    ct = O.query_encrypt(P, W.q_codes, W.q_masks, W.eye_ids)
+    Bq = O.query_extend(P, ct)
+    A = O.db_rows(P, W.db_codes, W.db_masks, ids)
+    Cm = O.ppmm(P.q, A, Bq)
+    F = O.fold(P, Cm, ids, n_eyes=W.q_codes.shape[0], n_real=W.db_codes.shape[0])
+    rc, rm = O.rotated_templates(W.q_codes, W.q_masks, P.rho)
+    num, den = O.hd_counts(rc, rm, O.unpack(W.db_codes), O.unpack(W.db_masks))
+    return dict(P=P, W=W, ids=ids, ct=ct, Bq=Bq, A=A, C=Cm, F=F, num=num, den=den,
+                inner=O.inner_from_counts(num, den))
+
+
+@pytest.fixture(scope="module")
+def gpu_run(tiny):
+    P, W = tiny["P"], tiny["W"]
+    eng = E.Engine(**E.TINY).keygen()
+    db = eng.encrypt_db(W.db_codes, W.db_masks, chunk_id=0)
+    ct = eng.encrypt_query(W.q_codes, W.q_masks, W.eye_ids)
+    q = eng.prepare(ct, W.q_codes.shape[0], "u64")
+    s = eng.match(db, q)
+    f = eng.fold(s)
+    dec = eng.decrypt(s)
+    fdec = eng.decrypt(f)
+    torch.cuda.synchronize()
+    return dict(eng=eng, db=db, ct=ct, q=q, s=s, f=f, dec=dec.cpu().numpy(), fdec=fdec.cpu().numpy())
+
+
+def test_primes(tiny, gpu_run):
+    assert gpu_run["eng"].primes == tiny["P"].q
+
+
+def test_query_ciphertext_bit_exact(tiny, gpu_run):
+    got = _u64(gpu_run["ct"], tiny["ct"].shape)
+    assert np.array_equal(got, tiny["ct"])
+
+
+def test_query_operand_bit_exact(tiny, gpu_run):
+    got = _u64(gpu_run["q"].buf, tiny["Bq"].shape)
+    assert np.array_equal(got, tiny["Bq"])
+
+
+def test_database_bit_exact(tiny, gpu_run):
+    A = tiny["A"]
+    assert gpu_run["db"].m_rows == A.shape[1]
+    got = _u64(gpu_run["db"].buf, A.shape)
+    assert np.array_equal(got, A)
+
+
+def test_ccmm_bit_exact(tiny, gpu_run):
+    got = gpu_run["s"].residues()
+    assert got.shape == tiny["C"].shape
+    assert np.array_equal(got, tiny["C"])
+
+
+@pytest.mark.parametrize("form", ["i8_digits", "i8_crt"])
+def test_ccmm_tensor_forms_bit_exact(tiny, gpu_run, form):
+    """The int8 tensor-core forms give the same residues as the oracle (and the u64 form)."""
+    eng, W = gpu_run["eng"], tiny["W"]
+    q = eng.prepare(gpu_run["ct"], W.q_codes.shape[0], form)
+    s = eng.match(gpu_run["db"], q)
+    torch.cuda.synchronize()
+    assert np.array_equal(s.residues(), tiny["C"])
+
+
+def test_fold_bit_exact(tiny, gpu_run):
+    got = gpu_run["f"].residues()
+    assert got.shape == tiny["F"].shape
+    assert np.array_equal(got, tiny["F"])
+
+
+def test_decrypted_numerators_exact(tiny, gpu_run):
+    assert np.array_equal(gpu_run["dec"], tiny["inner"])
+
+
+def test_decoded_distance_and_match_bits(tiny, gpu_run):
+    """Decoded fractional HD (numerator from the ciphertext, overlap ||m1 and m2|| from the
+    plaintext masks, Section 3) equals the FP64 cleartext HD; match bits are identical."""
+    num, den = tiny["num"], tiny["den"]
+    hd_clear = O.fractional_hd(num, den)
+    dec_num = (den.astype(np.int64) - gpu_run["dec"]) // 2          # <c1 xor c2, m1 and m2>
+    assert np.array_equal((den.astype(np.int64) - gpu_run["dec"]) % 2, np.zeros_like(den, dtype=np.int64))
+    hd_dec = O.fractional_hd(dec_num, den)
+    assert np.max(np.abs(hd_dec - hd_clear)) <= 2.0 ** -10
+    assert np.array_equal(O.match_bits(dec_num, den), O.match_bits(num, den))
+    # planted near-duplicates are found
+    mb = O.match_bits(num, den)
+    for row, (eye, _) in tiny["W"].planted.items():
+        assert mb[eye, row]
+
+
+def test_folded_decryption_is_cleartext_fold(tiny, gpu_run):
+    P, inner = tiny["P"], tiny["inner"]
+    n_db = inner.shape[1]
+    groups = [list(range(g, min(g + P.fold_k, P.rho))) for g in range(0, P.rho, P.fold_k)]
+    want = np.zeros((4 * len(groups), n_db), np.int64)
+    for e in range(4):
+        for g, grp in enumerate(groups):
+            for r in grp:
+                for i in range(n_db):
+                    src = i - r
+                    if src >= 0:
+                        want[e * len(groups) + g, i] += inner[e * P.rho + r, src]
+                    # wrapped sources are padding coefficients of the block (zero message)
+    assert np.array_equal(gpu_run["fdec"], want)
+
+
+# ------------------------------------------------------------------ plain modular product
+
+def _rand_res(rng, q, shape):
+    return np.stack([np.array(rng.integers(0, 1 << 62, size=shape, dtype=np.int64) % q_l, dtype=np.uint64)
+                     for q_l in q])
+
+
+FORMS = ["u64", "i8_digits", "i8_crt"]
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("M,N,K", [(1, 1, 1), (64, 64, 16), (65, 63, 17), (130, 37, 1000), (300, 5, 2049),
+                                   (7, 129, 64), (64, 1, 0), (0, 3, 5), (257, 70, 33)])
+def test_ppmm_ragged(form, M, N, K):
+    B.build()
+    rng = np.random.default_rng(M * 1000 + N * 10 + K)
+    q = [O.primes(60, 1)[0], O.primes(50, 1)[0], O.primes(31, 1, 64)[0]]
+    A = _rand_res(rng, q, (M, K))
+    Bm = _rand_res(rng, q, (N, K))
+    want = O.ppmm(q, A, Bm)
+    dA = torch.from_numpy(A.view(np.int64)).cuda()
+    dB = torch.from_numpy(Bm.view(np.int64)).cuda()
+    got = E.ppmm(form, q, dA, dB).cpu().numpy().view(np.uint64)
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("kind", ["minus_one", "digits_min"])
+def test_ppmm_extremes(form, kind):
+    """Deep K with operands at the accumulator limits.  minus_one: every residue q - 1.  digits_min:
+    the centred lift has its seven low balanced digits at -128, so every int8 digit product is
+    2^14 and a shift sums up to 7 pairs per column (the int32 accumulators must be chunked)."""
+    B.build()
+    q = O.primes(60, 2)
+    K = 24576
+    if kind == "minus_one":
+        xc = [-1, -1]
+    else:
+        v = -sum(128 * 256 ** t for t in range(7))
+        xc = [v, v]
+    A = np.stack([np.full((70, K), (x % q_l), np.uint64) for x, q_l in zip(xc, q)])
+    Bm = np.stack([np.full((9, K), (x % q_l), np.uint64) for x, q_l in zip(xc, q)])
+    got = E.ppmm(form, q, torch.from_numpy(A.view(np.int64)).cuda(),
+                 torch.from_numpy(Bm.view(np.int64)).cuda()).cpu().numpy().view(np.uint64)
+    for l, q_l in enumerate(q):
+        assert np.all(got[l] == (xc[l] * xc[l] * K) % q_l)

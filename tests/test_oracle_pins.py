@@ -329,7 +329,7 @@ def test_ccmm_decrypts_to_cleartext_inner_products(P):
         assert worst < 1e-3
     assert np.array_equal(dec, inner)
     # fold: decrypt(fold(C)) equals the cleartext fold of the numerators (negacyclic shifts)
-    F = O.fold(P, C, ids, n_eyes=2)
+    F = O.fold(P, C, ids, n_eyes=2, n_real=n_db)
     N = P.ndb
     groups = [list(range(g, min(g + P.fold_k, P.rho))) for g in range(0, P.rho, P.fold_k)]
     for e in range(2):
