@@ -172,9 +172,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="icm", choices=["icm", "reference"])
-    ap.add_argument("--form", default="i8_crt", choices=["u64", "i8_digits", "i8_crt", "f16_crt"])
-    ap.add_argument("--compare-forms", default="u64,i8_digits",
-                    help="comma list of other forms timed once each on the same workload ('' to skip)")
+    ap.add_argument("--form", default="f16_crt", choices=["u64", "i8_digits", "i8_crt", "f16_crt"])
+    ap.add_argument("--compare-forms", default="i8_crt,u64,i8_digits",
+                    help="comma list of other forms, each timed for one step on the same workload ('' to skip)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -219,19 +219,24 @@ def main():
         op = E._u8(C.icm_query_op_bytes(eng.ctx, N_EYES, f), dev)
         sc = E._u8(eng.scores_bytes(db, N_EYES, False), dev)
         fo = E._u8(eng.scores_bytes(db, N_EYES, True), dev)
+        mw = eng.match_workspace(db, N_EYES, form)
         evs = []
         t_start = torch.cuda.Event(enable_timing=True)
         t_end = torch.cuda.Event(enable_timing=True)
         with torch.cuda.stream(st):
+            if warmup == 0:
+                st.synchronize()
+                barrier()
+                t_start.record(st)
             for i in range(warmup + steps):
-                if i == warmup:
+                if i == warmup and warmup > 0:
                     st.synchronize()
                     barrier()
                     t_start.record(st)
                 e1, e2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 q = eng.prepare(ct, N_EYES, f, stream=st, out=op)
                 e1.record(st)
-                s = eng.match(db, q, stream=st, out=sc)
+                s = eng.match(db, q, stream=st, out=sc, ws=mw)
                 e2.record(st)
                 eng.fold(s, stream=st, out=fo)
                 if i >= warmup:
@@ -240,7 +245,7 @@ def main():
         st.synchronize()
         total_ms = t_start.elapsed_time(t_end)
         gemm_ms = [a.elapsed_time(b) for a, b in evs]
-        del op, sc, fo
+        del op, sc, fo, mw
         return total_ms, gemm_ms
 
     # ---- headline: K timed steps of the chosen form
@@ -265,28 +270,32 @@ def main():
         peak = 152 * 32 * sm_max * 1e6                      # 152 SMs x 32 IMAD.WIDE/clk x max SM clock
         roof = {"bound": "alu", "achieved": ops / gemm_avg_s / 1e9, "peak": peak / 1e9, "unit": "Gop/s",
                 "peak_source": "derived: 152 SMs x 32 IMAD.WIDE per clock x max SM clock"}
-    elif args.form in ("i8_digits", "i8_crt"):
+    elif args.form in ("i8_digits", "i8_crt", "f16_crt"):
         kp = (K + 31) // 32 * 32
+        esz = 2 if args.form == "f16_crt" else 1
         pairs = 64 if args.form == "i8_digits" else \
-            int((C.icm_query_op_bytes(eng.ctx, 1, f) - L * 31 * K * 8) // (L * 31 * kp))
+            int((C.icm_query_op_bytes(eng.ctx, 1, f) - L * 31 * K * 8) // (L * 31 * kp * esz))
         ops = 2.0 * pairs * M * n_cols * kp * L
-        peak = 2.0 * C.icm_probe_peak(1)
-        roof = {"bound": "tensor", "achieved": ops / gemm_avg_s / 1e12, "peak": peak / 1e12, "unit": "TOP/s",
-                "peak_source": "measured in this run: int8 mma.sync.m16n8k32 issue-bound probe (no tcgen05 int8 on sm_103a)"}
-    else:
-        ops = 0.0
-        peak = peaks.get("bf16_tflops", 1900.0) * 1e12
-        roof = {"bound": "tensor", "achieved": 0.0, "peak": peak / 1e12, "unit": "TFLOP/s", "peak_source": "measured bf16"}
+        if args.form == "f16_crt":
+            peak = 2.0 * C.icm_probe_peak(2)
+            roof = {"bound": "tensor", "achieved": ops / gemm_avg_s / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+                    "peak_source": "measured in this run: fp16 mma.sync.m16n8k16 issue-bound probe "
+                                   f"(MEASURED_PEAKS bf16 cuBLAS burst {peaks.get('bf16_tflops')} TFLOP/s uses tcgen05)"}
+        else:
+            peak = 2.0 * C.icm_probe_peak(1)
+            roof = {"bound": "tensor", "achieved": ops / gemm_avg_s / 1e12, "peak": peak / 1e12, "unit": "TOP/s",
+                    "peak_source": "measured in this run: int8 mma.sync.m16n8k32 issue-bound probe (no tcgen05 int8 on sm_103a)"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = NCU_TRAFFIC.get(args.form)
-    roof["kernel"] = {"u64": "k_ppmm_u64", "i8_digits": "k_ppmm_i8<0>", "i8_crt": "k_ppmm_i8<1>"}.get(args.form)
+    roof["kernel"] = {"u64": "k_ppmm_u64", "i8_digits": "k_ppmm_i8<0>", "i8_crt": "k_crt_p1<int8> + k_crt_combine",
+                      "f16_crt": "k_crt_p1<fp16> + k_crt_combine"}.get(args.form)
     roof["ms_per_launch"] = gemm_avg_s * 1e3
 
     # ---- other forms, one timed step each on the same workload
     forms = {args.form: {"value": value, "ms_per_step": ms_per_step}}
     for other in [x for x in args.compare_forms.split(",") if x and x != args.form]:
-        tot, gm = timed_form(other, 1, 1)
-        forms[other] = {"value": comps / (tot / 1e3), "ms_per_step": tot}
+        tot, gm = timed_form(other, 1, 0)          # one step (first launch of that form)
+        forms[other] = {"value": comps / (tot / 1e3), "ms_per_step": tot, "gemm_ms": gm[0]}
 
     # ---- end to end through the C ABI with host buffers
     f = C.FORMS[args.form]
@@ -315,7 +324,9 @@ def main():
            "d2h_bytes_per_step": fo_bytes, "ms_per_step": te.item()}
     del wsbuf
 
-    launches_per_step = 1 + (1 if args.form != "u64" else 0) + 1 + 1
+    n_chunks = (N_EYES * 31 + 511) // 512
+    launches_per_step = 1 + (1 if args.form != "u64" else 0) + \
+        (2 * n_chunks if args.form in ("i8_crt", "f16_crt") else 1) + 1
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": max(args.warmup, 1), "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.form], "data": "synthetic",

@@ -61,8 +61,9 @@ typedef enum {
                                 products per digit pair, int32 accumulation, fused recombination */
     ICM_FORM_I8_CRT = 2,     /* residues split over small pairwise-coprime moduli (<= 256),
                                 int8 tensor-core product per modulus, exact CRT back mod q_l  */
-    ICM_FORM_F16_CRT = 3     /* small-modulus residues as exact fp16 integers on tcgen05 tensor
-                                cores with fp32 TMEM accumulation flushed before 2^24          */
+    ICM_FORM_F16_CRT = 3     /* small-modulus residues as exact fp16 integers on fp16 tensor
+                                cores, fp32 accumulation reduced modulo m_i before it reaches
+                                2^24, residues recombined by CRT in a second pass             */
 } icm_form;
 
 typedef struct icm_ctx icm_ctx;
@@ -149,11 +150,16 @@ void icm_query_destroy(icm_query *q);
 /* Bytes of the encrypted scores of one chunk for n_eyes eyes (folded != 0: after the fold). */
 icm_status icm_scores_bytes(const icm_ctx *ctx, const icm_db *db, size_t n_eyes, int folded, size_t *bytes);
 
+/* Device workspace bytes that icm_match needs for a form (0 for u64 and the int8 forms; the
+ * fp16 CRT form keeps one byte per output residue and modulus). */
+icm_status icm_match_workspace_bytes(const icm_ctx *ctx, const icm_db *db, size_t n_eyes, icm_form form, size_t *bytes);
+
 /* CCMM (Section 2.3): C = [A1 A2; B1 B2] * [B_q; A_q] per limb, i.e. the four plaintext modular
  * products fused into one [M x K] x [K x d3] product per RNS limb, in the query's form.  Output
- * bit-identical across forms.  dev_out: icm_scores_bytes(folded = 0). */
+ * bit-identical across forms.  dev_out: icm_scores_bytes(folded = 0); dev_ws:
+ * icm_match_workspace_bytes bytes (may be NULL when that is 0). */
 icm_status icm_match(icm_ctx *ctx, const icm_db *db, const icm_query *q, void *dev_out, size_t bytes,
-                     void *stream, icm_scores **out);
+                     void *dev_ws, size_t ws_bytes, void *stream, icm_scores **out);
 
 /* Fold (Algorithm 2, linear key-free part): for eye e and group g of fold_k rotations,
  * ct'_{e,g} = sum_{r in g} X^r * ct_{e,r} on the a-part and every b-block polynomial; the shift

@@ -342,10 +342,12 @@ icm_status icm_query_op_bytes(const icm_ctx *c, size_t n_eyes, icm_form form, si
     switch (form) {
         case ICM_FORM_U64: *bytes = n * 8; return ICM_OK;
         case ICM_FORM_I8_DIGITS:
-        case ICM_FORM_I8_CRT: {
-            if (form == ICM_FORM_I8_CRT && !c->i8_crt_ok) return fail(ICM_EBOUND, "CRT form unavailable for these primes / K");
+        case ICM_FORM_I8_CRT:
+        case ICM_FORM_F16_CRT: {
+            if (form != ICM_FORM_I8_DIGITS && !c->i8_crt_ok) return fail(ICM_EBOUND, "CRT form unavailable for these primes / K");
             const uint32_t P = form == ICM_FORM_I8_DIGITS ? 8 : c->i8_crt.n_mod;
-            *bytes = n * 8 + (size_t)c->p.n_limbs * P * n_eyes * c->p.rho * i8_kpad(c->K);
+            const size_t esz = form == ICM_FORM_F16_CRT ? 2 : 1;
+            *bytes = n * 8 + (size_t)c->p.n_limbs * P * n_eyes * c->p.rho * i8_kpad(c->K) * esz;
             return ICM_OK;
         }
         default: return fail(ICM_EUNSUPPORTED, "form not built");
@@ -363,10 +365,14 @@ icm_status icm_query_prepare(icm_ctx *c, const void *dev_ct, size_t n_eyes, icm_
     if (!q) return fail(ICM_ENOMEM, "host allocation");
     const uint32_t n_cols = (uint32_t)(n_eyes * c->p.rho);
     cudaError_t e = launch_query_extend(c, (const uint64_t *)dev_ct, n_cols, (uint64_t *)dev_op, (cudaStream_t)stream);
-    if (e == cudaSuccess && (form == ICM_FORM_I8_DIGITS || form == ICM_FORM_I8_CRT)) {
+    if (e == cudaSuccess && form != ICM_FORM_U64) {
         const I8Consts &k = form == ICM_FORM_I8_DIGITS ? c->i8_digits : c->i8_crt;
         int8_t *planes = (int8_t *)dev_op + (size_t)c->p.n_limbs * n_cols * c->K * 8;
-        e = launch_planes(form, k, (const uint64_t *)dev_op, planes, n_cols, c->K, i8_kpad(c->K), (cudaStream_t)stream);
+        if (form == ICM_FORM_I8_DIGITS)
+            e = launch_planes(form, k, (const uint64_t *)dev_op, planes, n_cols, c->K, i8_kpad(c->K), (cudaStream_t)stream);
+        else
+            e = launch_crt_planes(form == ICM_FORM_F16_CRT, k, (const uint64_t *)dev_op, planes, n_cols, c->K, i8_kpad(c->K),
+                                  (cudaStream_t)stream);
     }
     if (e != cudaSuccess) { delete q; return fail(ICM_ECUDA, std::string("query prepare: ") + cudaGetErrorString(e)); }
     q->ctx = c; q->form = form; q->n_eyes = (uint32_t)n_eyes; q->n_cols = n_cols; q->dev = dev_op; q->bytes = bytes;
@@ -383,12 +389,21 @@ icm_status icm_scores_bytes(const icm_ctx *c, const icm_db *db, size_t n_eyes, i
     return ICM_OK;
 }
 
-icm_status icm_match(icm_ctx *c, const icm_db *db, const icm_query *q, void *dev_out, size_t bytes, void *stream,
-                     icm_scores **out) {
+icm_status icm_match_workspace_bytes(const icm_ctx *c, const icm_db *db, size_t n_eyes, icm_form form, size_t *bytes) {
+    if (!c || !db || !bytes) return fail(ICM_EINVAL, "null argument");
+    const bool crt = form == ICM_FORM_F16_CRT || form == ICM_FORM_I8_CRT;
+    *bytes = crt ? crt_scratch_bytes(c->p.n_limbs, c->i8_crt.n_mod, (uint64_t)n_eyes * c->p.rho, db->lay.M) : 0;
+    return ICM_OK;
+}
+
+icm_status icm_match(icm_ctx *c, const icm_db *db, const icm_query *q, void *dev_out, size_t bytes, void *dev_ws,
+                     size_t ws_bytes, void *stream, icm_scores **out) {
     if (!c || !db || !q || !dev_out || !out) return fail(ICM_EINVAL, "null argument");
     if (db->ctx != c || q->ctx != c) return fail(ICM_EINVAL, "handles from another context");
     size_t need; icm_scores_bytes(c, db, q->n_eyes, 0, &need);
     if (bytes < need) return fail(ICM_ENOMEM, "scores buffer too small");
+    size_t wneed; icm_match_workspace_bytes(c, db, q->n_eyes, q->form, &wneed);
+    if (wneed && (!dev_ws || ws_bytes < wneed)) return fail(ICM_ENOMEM, "match workspace too small");
     icm_scores *sc = new (std::nothrow) icm_scores();
     if (!sc) return fail(ICM_ENOMEM, "host allocation");
     cudaError_t e = cudaSuccess;
@@ -397,12 +412,17 @@ icm_status icm_match(icm_ctx *c, const icm_db *db, const icm_query *q, void *dev
             e = launch_ppmm_u64(c->lt, db->dev, (const uint64_t *)q->dev, (uint64_t *)dev_out, db->lay.M, q->n_cols, c->K,
                                 (cudaStream_t)stream);
             break;
-        case ICM_FORM_I8_DIGITS:
-        case ICM_FORM_I8_CRT: {
-            const I8Consts &k = q->form == ICM_FORM_I8_DIGITS ? c->i8_digits : c->i8_crt;
+        case ICM_FORM_I8_DIGITS: {
             const int8_t *planes = (const int8_t *)q->dev + (size_t)c->p.n_limbs * q->n_cols * c->K * 8;
-            e = launch_ppmm_i8(q->form, k, db->dev, planes, (uint64_t *)dev_out, db->lay.M, q->n_cols, c->K, i8_kpad(c->K),
-                               (cudaStream_t)stream);
+            e = launch_ppmm_i8(q->form, c->i8_digits, db->dev, planes, (uint64_t *)dev_out, db->lay.M, q->n_cols, c->K,
+                               i8_kpad(c->K), (cudaStream_t)stream);
+            break;
+        }
+        case ICM_FORM_I8_CRT:
+        case ICM_FORM_F16_CRT: {
+            const void *planes = (const char *)q->dev + (size_t)c->p.n_limbs * q->n_cols * c->K * 8;
+            e = launch_ppmm_crt(q->form == ICM_FORM_F16_CRT, c->crt_bn, c->i8_crt, db->dev, planes, (uint64_t *)dev_out,
+                                db->lay.M, q->n_cols, c->K, i8_kpad(c->K), dev_ws, (cudaStream_t)stream);
             break;
         }
         default: delete sc; return fail(ICM_EUNSUPPORTED, "form not built");
@@ -455,20 +475,21 @@ static size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 icm_status icm_match_host_workspace_bytes(const icm_ctx *c, const icm_db *db, size_t n_eyes, icm_form form,
                                           size_t *bytes) {
     if (!c || !db || !bytes) return fail(ICM_EINVAL, "null argument");
-    size_t ct, op, sc, fo;
+    size_t ct, op, sc, fo, mw;
     icm_status s;
     if ((s = icm_query_ct_bytes(c, n_eyes, &ct)) != ICM_OK) return s;
     if ((s = icm_query_op_bytes(c, n_eyes, form, &op)) != ICM_OK) return s;
     if ((s = icm_scores_bytes(c, db, n_eyes, 0, &sc)) != ICM_OK) return s;
     if ((s = icm_scores_bytes(c, db, n_eyes, 1, &fo)) != ICM_OK) return s;
-    *bytes = align256(ct) + align256(op) + align256(sc) + align256(fo);
+    if ((s = icm_match_workspace_bytes(c, db, n_eyes, form, &mw)) != ICM_OK) return s;
+    *bytes = align256(ct) + align256(op) + align256(sc) + align256(fo) + align256(mw);
     return ICM_OK;
 }
 
 icm_status icm_match_host(icm_ctx *c, const icm_db *db, const uint64_t *host_ct, size_t n_eyes, icm_form form,
                           uint64_t *host_folded, void *dev_ws, size_t ws_bytes, void *stream) {
     if (!c || !db || !host_ct || !host_folded || !dev_ws) return fail(ICM_EINVAL, "null argument");
-    size_t need, ct, op, sc, fo;
+    size_t need, ct, op, sc, fo, mw;
     icm_status s = icm_match_host_workspace_bytes(c, db, n_eyes, form, &need);
     if (s != ICM_OK) return s;
     if (ws_bytes < need) return fail(ICM_ENOMEM, "workspace too small");
@@ -476,15 +497,17 @@ icm_status icm_match_host(icm_ctx *c, const icm_db *db, const uint64_t *host_ct,
     icm_query_op_bytes(c, n_eyes, form, &op);
     icm_scores_bytes(c, db, n_eyes, 0, &sc);
     icm_scores_bytes(c, db, n_eyes, 1, &fo);
+    icm_match_workspace_bytes(c, db, n_eyes, form, &mw);
     char *w = (char *)dev_ws;
     void *d_ct = w, *d_op = w + align256(ct), *d_sc = w + align256(ct) + align256(op);
     void *d_fo = w + align256(ct) + align256(op) + align256(sc);
+    void *d_mw = w + align256(ct) + align256(op) + align256(sc) + align256(fo);
     cudaStream_t st = (cudaStream_t)stream;
     CUDA_TRY(cudaMemcpyAsync(d_ct, host_ct, ct, cudaMemcpyHostToDevice, st));
     icm_query *q = nullptr;
     icm_scores *m = nullptr, *f = nullptr;
     if ((s = icm_query_prepare(c, d_ct, n_eyes, form, d_op, op, stream, &q)) != ICM_OK) return s;
-    s = icm_match(c, db, q, d_sc, sc, stream, &m);
+    s = icm_match(c, db, q, d_sc, sc, mw ? d_mw : nullptr, mw, stream, &m);
     if (s == ICM_OK) s = icm_fold(c, m, d_fo, fo, stream, &f);
     icm_query_destroy(q);
     icm_scores_destroy(m);
@@ -495,16 +518,18 @@ icm_status icm_match_host(icm_ctx *c, const icm_db *db, const uint64_t *host_ct,
 }
 
 icm_status icm_ppmm_workspace_bytes(icm_form form, uint32_t n_limbs, size_t M, size_t N, size_t K, size_t *bytes) {
-    (void)M;
     if (!bytes) return fail(ICM_EINVAL, "null argument");
     switch (form) {
         case ICM_FORM_U64: *bytes = 0; return ICM_OK;
         case ICM_FORM_I8_DIGITS:
-        case ICM_FORM_I8_CRT: {
+        case ICM_FORM_I8_CRT:
+        case ICM_FORM_F16_CRT: {
             // sized for the worst case of primes just below 2^60
-            const uint32_t P = i8_planes(form, std::vector<uint64_t>{(1ull << 60) - 1}, K);
+            const int pf = form == ICM_FORM_F16_CRT ? (int)ICM_FORM_I8_CRT : (int)form;
+            const uint32_t P = i8_planes(pf, std::vector<uint64_t>{(1ull << 60) - 1}, K);
             if (!P) return fail(ICM_EBOUND, "CRT form unavailable for this K");
-            *bytes = (size_t)n_limbs * P * N * i8_kpad(K);
+            *bytes = (size_t)n_limbs * P * N * i8_kpad(K) * (form == ICM_FORM_F16_CRT ? 2 : 1);
+            if (form != ICM_FORM_I8_DIGITS) *bytes += 256 + crt_scratch_bytes(n_limbs, P, N, M);
             return ICM_OK;
         }
         default: return fail(ICM_EUNSUPPORTED, "form not built");
@@ -525,18 +550,30 @@ icm_status icm_ppmm(icm_form form, const uint64_t *q, uint32_t n_limbs, const ui
     cudaError_t e;
     switch (form) {
         case ICM_FORM_U64: e = launch_ppmm_u64(lt, dev_A, dev_B, dev_C, M, N, K, (cudaStream_t)stream); break;
-        case ICM_FORM_I8_DIGITS:
-        case ICM_FORM_I8_CRT: {
+        case ICM_FORM_I8_DIGITS: {
             I8Consts k;
             const char *why = "";
             if (!make_i8_consts(form, qv, K, k, &why)) return fail(ICM_EBOUND, why);
-            size_t need = 0;
-            icm_ppmm_workspace_bytes(form, n_limbs, M, N, K, &need);
-            const size_t P = form == ICM_FORM_I8_DIGITS ? 8 : k.n_mod;
-            if (!dev_ws || ws_bytes < (size_t)n_limbs * P * N * i8_kpad(K)) return fail(ICM_ENOMEM, "workspace too small");
+            const size_t pl = (size_t)n_limbs * 8 * N * i8_kpad(K);
+            if (pl && (!dev_ws || ws_bytes < pl)) return fail(ICM_ENOMEM, "workspace too small");
             e = launch_planes(form, k, dev_B, (int8_t *)dev_ws, N, K, i8_kpad(K), (cudaStream_t)stream);
             if (e == cudaSuccess)
                 e = launch_ppmm_i8(form, k, dev_A, (const int8_t *)dev_ws, dev_C, M, N, K, i8_kpad(K), (cudaStream_t)stream);
+            break;
+        }
+        case ICM_FORM_I8_CRT:
+        case ICM_FORM_F16_CRT: {
+            I8Consts k;
+            const char *why = "";
+            if (!make_i8_consts(ICM_FORM_I8_CRT, qv, K, k, &why)) return fail(ICM_EBOUND, why);
+            const bool f16 = form == ICM_FORM_F16_CRT;
+            const size_t pl = (size_t)n_limbs * k.n_mod * N * i8_kpad(K) * (f16 ? 2 : 1);
+            const size_t sc = crt_scratch_bytes(n_limbs, k.n_mod, N, M);
+            if ((pl || sc) && (!dev_ws || ws_bytes < align256(pl) + sc)) return fail(ICM_ENOMEM, "workspace too small");
+            e = launch_crt_planes(f16, k, dev_B, dev_ws, N, K, i8_kpad(K), (cudaStream_t)stream);
+            if (e == cudaSuccess)
+                e = launch_ppmm_crt(f16, 256, k, dev_A, dev_ws, dev_C, M, N, K, i8_kpad(K), (char *)dev_ws + align256(pl),
+                                    (cudaStream_t)stream);
             break;
         }
         default: return fail(ICM_EUNSUPPORTED, "form not built");

@@ -1,0 +1,338 @@
+// Plaintext modular matrix product over a small-modulus RNS on tensor cores (Section 6.2.2: the
+// modular products are reduced to int8 GEMMs through an RNS of small moduli below 2^8).  Used by
+// the forms ICM_FORM_I8_CRT (int8 operands, mma.sync m16n8k32 s8 -> s32) and ICM_FORM_F16_CRT
+// (the same residues held exactly as fp16, mma.sync m16n8k16 f16 -> f32; GB300 issues fp16 tensor
+// products at about four times its int8 rate).
+//
+// For r pairwise-coprime moduli m_i <= 256 with product M > 2^9 K ((q-1)/2)^2:
+//  phase 1 (one block per limb, modulus, 128-row tile and column tile): c_i = C mod m_i with
+//    C = sum_k a[k] b[k] over the centred residues a = A mod m_i, b = B mod m_i (|x| <= 128) of
+//    the centred lifts of A and B.  int8: int32 accumulation is exact (K 2^14 < 2^31).  fp16:
+//    products <= 2^14 are exact in fp32 and the fp32 sum stays an exact integer below 2^24, so it
+//    is reduced modulo m_i every 512 columns of K (512 * 2^14 + 128 < 2^24).  c_i goes to a byte
+//    scratch.
+//  phase 2 (one thread per output): C mod q = sum_i y_i (M/m_i mod q) - kappa (M mod q) with
+//    y_i = c_i (M/m_i)^-1 mod m_i and kappa = round(sum_i y_i / m_i) (|C| / M < 2^-9, so fp32
+//    decides kappa exactly).
+//
+// Phase 1 tiling: 128 x BN tile per 256-thread block (2 x 4 warps, 64 x BN/4 each), K in slabs of
+// 32 values.  The database residues are formed on the fly from the canonical u64 (centred lift,
+// balanced base-256 digits, two dp4a against the centred constants 256^t mod m_i, one rounding
+// step) and stored to shared memory; the next slab is loaded into registers while the current
+// one is multiplied.  The query planes stream in with cp.async.  Fragments come from ldmatrix on
+// rows padded by 16 bytes (conflict-free).  Blocks of one (limb, row tile) are consecutive in
+// launch order (column tiles, then moduli, vary fastest) so a database slab is read from HBM
+// about once and re-served from L2.  Columns are processed in chunks so the scratch stays at
+// L r min(N, 512) M bytes.
+#include "icm_internal.h"
+#include "ppmm_i8.h"
+
+#include <algorithm>
+#include <cuda_fp16.h>
+
+namespace {
+
+constexpr int BM = 128, KS = 32, NT = 256, FLUSH = 512;
+constexpr uint64_t NCHUNK = 512;            // columns per phase-1/phase-2 round
+
+struct P1Args {
+    const uint64_t *A;       // [L][M][K]
+    const void *Bp;          // [L][r][N][Kp] int8 or fp16 planes
+    uint8_t *R;              // [L][r][nch][M] scratch
+    uint64_t M, N, K, Kp, n0, nch;
+    uint32_t n_ntile;
+    icm::I8Consts k;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void ldsm_x4(uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3, uint32_t addr) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(addr));
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, bool pred) {
+    const int n = pred ? 16 : 0;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" :: "r"(dst), "l"(src), "r"(n));
+}
+
+template <bool F16>
+struct Acc;
+template <>
+struct Acc<true> { using T = float; };
+template <>
+struct Acc<false> { using T = int; };
+
+__device__ __forceinline__ void mma(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+__device__ __forceinline__ void mma(int (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+    asm volatile("mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+                 : "+r"(c[0]), "+r"(c[1]), "+r"(c[2]), "+r"(c[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// Centred residue (|r| <= m/2 + 1) of the centred lift of x modulo m: the bytes of
+// lift(x) + 0x80..80 are the balanced digits d_t + 128, and lift(x) = sum_t d_t 256^t, so two dp4a
+// against the centred constants w_t = 256^t mod m give a representative of |s| <= 2^17.
+__device__ __forceinline__ int crt_residue(uint64_t x, uint64_t q, int m, int wlo, int whi, float inv_m) {
+    const uint64_t y = ((x > (q >> 1)) ? x - q : x) + 0x8080808080808080ull;
+    int s = __dp4a((int)((uint32_t)y ^ 0x80808080u), wlo, 0);
+    s = __dp4a((int)((uint32_t)(y >> 32) ^ 0x80808080u), whi, s);
+    return s - m * __float2int_rn((float)s * inv_m);
+}
+
+// 4 residues -> packed operand bits (int8: one word, fp16: two words)
+template <bool F16>
+__device__ __forceinline__ void pack4(const int (&v)[4], uint32_t (&w)[2]) {
+    if (F16) {
+        __half2 h01 = __halves2half2(__int2half_rn(v[0]), __int2half_rn(v[1]));
+        __half2 h23 = __halves2half2(__int2half_rn(v[2]), __int2half_rn(v[3]));
+        w[0] = *reinterpret_cast<uint32_t *>(&h01);
+        w[1] = *reinterpret_cast<uint32_t *>(&h23);
+    } else {
+        w[0] = (uint32_t)(v[0] & 0xFF) | ((uint32_t)(v[1] & 0xFF) << 8) | ((uint32_t)(v[2] & 0xFF) << 16) |
+               ((uint32_t)(v[3] & 0xFF) << 24);
+        w[1] = 0;
+    }
+}
+
+template <bool F16, int BN>
+__global__ void __launch_bounds__(NT, 1) k_crt_p1(P1Args p) {
+    constexpr int ESZ = F16 ? 2 : 1;              // operand bytes
+    constexpr int ROWB = KS * ESZ;                // bytes of one row of a slab
+    constexpr int LDB = ROWB + 16;                // padded row stride (bytes)
+    constexpr int STEPS = ROWB / 32;              // mma k-steps per slab (32 operand bytes each)
+    constexpr int WN = BN / 4;                    // warp tile columns
+    constexpr int NT8 = WN / 8;
+    using AccT = typename Acc<F16>::T;
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned char *sA = smem;                                   // [2][BM][LDB]
+    unsigned char *sB = smem + 2 * BM * LDB;                    // [2][BN][LDB]
+
+    const uint32_t nt = blockIdx.x % p.n_ntile, mi = blockIdx.x / p.n_ntile;
+    const uint32_t l = blockIdx.z;
+    const uint64_t m0 = (uint64_t)blockIdx.y * BM, nb = (uint64_t)nt * BN;   // nb: column within the chunk
+    const uint64_t M = p.M, N = p.N, K = p.K, Kp = p.Kp;
+    const uint32_t r = p.k.n_mod;
+    const int m = p.k.mod[mi], wlo = p.k.wlo[mi], whi = p.k.whi[mi];
+    const float inv_m = p.k.inv_m[mi];
+    const uint64_t q = p.k.q[l];
+    const uint64_t *Al = p.A + (size_t)l * M * K;
+    const unsigned char *Bl = reinterpret_cast<const unsigned char *>(p.Bp) + (((size_t)l * r + mi) * N + p.n0) * Kp * ESZ;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp & 1, wn = warp >> 1;
+
+    AccT acc[4][NT8][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < NT8; ++b)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[a][b][c] = 0;
+
+    uint64_t ra[4][4];                            // prefetched slab: 4 groups of 4 consecutive k
+    auto load_a = [&](uint64_t k0) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int idx = tid + e * NT, row = idx >> 3, g = idx & 7;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint64_t k = k0 + g * 4 + j;
+                ra[e][j] = (m0 + row < M && k < K) ? __ldg(Al + (m0 + row) * K + k) : 0ull;
+            }
+        }
+    };
+    auto store_a = [&](int st) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int idx = tid + e * NT, row = idx >> 3, g = idx & 7;
+            int v[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) v[j] = crt_residue(ra[e][j], q, m, wlo, whi, inv_m);
+            uint32_t w[2];
+            pack4<F16>(v, w);
+            unsigned char *dst = sA + (size_t)st * BM * LDB + row * LDB + g * 4 * ESZ;
+            if (F16) *reinterpret_cast<uint2 *>(dst) = make_uint2(w[0], w[1]);
+            else *reinterpret_cast<uint32_t *>(dst) = w[0];
+        }
+    };
+    constexpr int CH = ROWB / 16;                 // 16-byte chunks per column per slab
+    auto load_b = [&](int st, uint64_t k0) {
+#pragma unroll
+        for (int e = 0; e < (BN * CH) / NT; ++e) {
+            const int idx = tid + e * NT, col = idx / CH, ch = idx % CH;
+            const bool ok = p.n0 + nb + col < N && nb + col < p.nch;
+            const unsigned char *src = Bl + (ok ? ((nb + col) * Kp + k0) * ESZ + ch * 16 : 0);
+            cp_async16(smem_u32(sB + (size_t)st * BN * LDB + col * LDB + ch * 16), src, ok);
+        }
+        asm volatile("cp.async.commit_group;");
+    };
+
+    const uint64_t nk = (K + KS - 1) / KS;
+    if (nk > 0) {
+        load_a(0);
+        load_b(0, 0);
+        store_a(0);
+        asm volatile("cp.async.wait_group 0;");
+        __syncthreads();
+    }
+    for (uint64_t kt = 0; kt < nk; ++kt) {
+        const int st = (int)(kt & 1);
+        const bool more = kt + 1 < nk;
+        if (more) { load_a((kt + 1) * KS); load_b(st ^ 1, (kt + 1) * KS); }
+        const unsigned char *a_s = sA + (size_t)st * BM * LDB, *b_s = sB + (size_t)st * BN * LDB;
+#pragma unroll
+        for (int ks = 0; ks < STEPS; ++ks) {
+            uint32_t af[4][4], bf[NT8][2];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const int row = wm * 64 + a * 16 + (lane & 15);
+                ldsm_x4(af[a][0], af[a][1], af[a][2], af[a][3], smem_u32(a_s + row * LDB + ks * 32 + (lane >> 4) * 16));
+            }
+#pragma unroll
+            for (int b = 0; b < NT8; b += 2) {
+                const int ncol = wn * WN + b * 8 + (lane & 7) + ((lane >> 4) << 3);
+                ldsm_x4(bf[b][0], bf[b][1], bf[b + 1][0], bf[b + 1][1],
+                        smem_u32(b_s + ncol * LDB + ks * 32 + ((lane >> 3) & 1) * 16));
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < NT8; ++b) mma(acc[a][b], af[a], bf[b]);
+        }
+        if (F16 && ((kt + 1) * KS) % FLUSH == 0) {
+            const float fm = (float)m;
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < NT8; ++b)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        float &x = reinterpret_cast<float &>(acc[a][b][c]);
+                        x = fmaf(-fm, rintf(x * inv_m), x);
+                    }
+        }
+        if (more) store_a(st ^ 1);
+        asm volatile("cp.async.wait_group 0;");
+        __syncthreads();
+    }
+
+    // c_i in [0, m) to the scratch, column-major within the chunk
+    const int g = lane >> 2, tq = lane & 3;
+    uint8_t *Rl = p.R + ((size_t)l * r + mi) * p.nch * M;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < NT8; ++b)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const uint64_t row = m0 + wm * 64 + a * 16 + g + (c >> 1) * 8;
+                const uint64_t col = nb + wn * WN + b * 8 + tq * 2 + (c & 1);
+                if (row >= M || col >= p.nch || p.n0 + col >= N) continue;
+                int v;
+                if (F16) v = __float2int_rn(reinterpret_cast<const float &>(acc[a][b][c])) % m;
+                else v = reinterpret_cast<const int &>(acc[a][b][c]) % m;
+                v = v < 0 ? v + m : v;
+                Rl[col * M + row] = (uint8_t)v;
+            }
+}
+
+struct P2Args {
+    const uint8_t *R;        // [L][r][nch][M]
+    uint64_t *C;             // [L][N][M]
+    uint64_t M, N, n0, nch;
+    icm::I8Consts k;
+};
+
+__global__ void __launch_bounds__(256) k_crt_combine(P2Args p) {
+    const uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;   // within the chunk
+    const uint32_t l = blockIdx.y;
+    const uint64_t cnt = p.nch * p.M;
+    if (idx >= cnt) return;
+    const uint32_t r = p.k.n_mod;
+    const uint64_t q = p.k.q[l];
+    const uint8_t *Rl = p.R + (size_t)l * r * cnt + idx;
+    uint64_t S = 0;
+    float F = 0.f;
+    for (uint32_t i = 0; i < r; ++i) {
+        const uint32_t c = Rl[(size_t)i * cnt];
+        const uint32_t y = (c * (uint32_t)p.k.yinv[i]) % (uint32_t)p.k.mod[i];
+        S = add_mod(S, mulmod_shoup(y, p.k.W[l][i], p.k.Ws[l][i], q), q);
+        F += (float)y * p.k.inv_m[i];
+    }
+    const uint64_t kappa = (uint64_t)__float2int_rn(F);
+    p.C[((size_t)l * p.N + p.n0) * p.M + idx] = sub_mod(S, mulmod_shoup(kappa, p.k.Mq[l], p.k.Mqs[l], q), q);
+}
+
+// Residue planes of the query operand: [L][r][N][Kp] (int8 or fp16), zero padded.
+template <bool F16>
+__global__ void __launch_bounds__(256) k_crt_planes(const uint64_t *op, void *planes, uint64_t N, uint64_t K, uint64_t Kp,
+                                                    icm::I8Consts k) {
+    const uint32_t l = blockIdx.y;
+    const uint32_t r = k.n_mod;
+    const uint64_t q = k.q[l];
+    const uint64_t total = N * Kp;
+    for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t j = idx / Kp, kk = idx % Kp;
+        const uint64_t v = kk < K ? op[((size_t)l * N + j) * K + kk] : 0;
+        for (uint32_t i = 0; i < r; ++i) {
+            const int res = crt_residue(v, q, k.mod[i], k.wlo[i], k.whi[i], k.inv_m[i]);
+            const size_t o = ((size_t)l * r + i) * total + idx;
+            if (F16) reinterpret_cast<__half *>(planes)[o] = __int2half_rn(res);
+            else reinterpret_cast<int8_t *>(planes)[o] = (int8_t)res;
+        }
+    }
+}
+
+template <bool F16, int BN>
+cudaError_t run_p1(const P1Args &a, cudaStream_t st) {
+    constexpr int LDB = KS * (F16 ? 2 : 1) + 16;
+    const size_t smem = (size_t)2 * (BM + BN) * LDB;
+    cudaError_t e = cudaFuncSetAttribute(k_crt_p1<F16, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid(a.n_ntile * a.k.n_mod, (unsigned)((a.M + BM - 1) / BM), a.k.n_limbs);
+    k_crt_p1<F16, BN><<<grid, NT, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+namespace icm {
+
+uint64_t crt_scratch_bytes(uint32_t n_limbs, uint32_t n_mod, uint64_t N, uint64_t M) {
+    return (uint64_t)n_limbs * n_mod * std::min<uint64_t>(N, NCHUNK) * M;
+}
+
+cudaError_t launch_crt_planes(bool f16, const I8Consts &k, const uint64_t *op, void *planes, uint64_t N, uint64_t K,
+                              uint64_t Kp, cudaStream_t st) {
+    if (N == 0 || Kp == 0) return cudaSuccess;
+    const uint64_t total = N * Kp;
+    const unsigned blocks = (unsigned)std::min<uint64_t>((total + 255) / 256, 152u * 32u);
+    if (f16) k_crt_planes<true><<<dim3(blocks, k.n_limbs), 256, 0, st>>>(op, planes, N, K, Kp, k);
+    else k_crt_planes<false><<<dim3(blocks, k.n_limbs), 256, 0, st>>>(op, planes, N, K, Kp, k);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ppmm_crt(bool f16, int bn, const I8Consts &k, const uint64_t *A, const void *Bp, uint64_t *C,
+                            uint64_t M, uint64_t N, uint64_t K, uint64_t Kp, void *scratch, cudaStream_t st) {
+    if (M == 0 || N == 0) return cudaSuccess;
+    for (uint64_t n0 = 0; n0 < N; n0 += NCHUNK) {
+        const uint64_t nch = std::min<uint64_t>(NCHUNK, N - n0);
+        P1Args a{A, Bp, reinterpret_cast<uint8_t *>(scratch), M, N, K, Kp, n0, nch,
+                 (uint32_t)((nch + bn - 1) / bn), k};
+        cudaError_t e;
+        if (f16) e = bn == 128 ? run_p1<true, 128>(a, st) : run_p1<true, 256>(a, st);
+        else e = bn == 128 ? run_p1<false, 128>(a, st) : run_p1<false, 256>(a, st);
+        if (e != cudaSuccess) return e;
+        P2Args b{reinterpret_cast<const uint8_t *>(scratch), C, M, N, n0, nch, k};
+        k_crt_combine<<<dim3((unsigned)((nch * M + 255) / 256), k.n_limbs), 256, 0, st>>>(b);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace icm

@@ -262,8 +262,7 @@ cudaError_t launch_planes(int form, const I8Consts &k, const uint64_t *op, int8_
     const uint64_t total = N * Kp;
     const unsigned blocks = (unsigned)std::min<uint64_t>((total + 255) / 256, 152u * 32u);
     dim3 grid(blocks, k.n_limbs);
-    if (form == ICM_FORM_I8_DIGITS) k_planes<0><<<grid, 256, 0, st>>>(op, planes, N, K, Kp, k);
-    else k_planes<1><<<grid, 256, 0, st>>>(op, planes, N, K, Kp, k);
+    k_planes<0><<<grid, 256, 0, st>>>(op, planes, N, K, Kp, k);
     return cudaGetLastError();
 }
 
@@ -272,8 +271,7 @@ cudaError_t launch_ppmm_i8(int form, const I8Consts &k, const uint64_t *A, const
     if (M == 0 || N == 0) return cudaSuccess;
     I8Args a{A, Bp, C, M, N, K, Kp, k};
     dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((N + BN - 1) / BN), k.n_limbs);
-    if (form == ICM_FORM_I8_DIGITS) k_ppmm_i8<0><<<grid, NT, 0, st>>>(a);
-    else k_ppmm_i8<1><<<grid, NT, 0, st>>>(a);
+    k_ppmm_i8<0><<<grid, NT, 0, st>>>(a);
     return cudaGetLastError();
 }
 

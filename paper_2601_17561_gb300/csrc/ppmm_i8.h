@@ -32,6 +32,12 @@ inline uint64_t i8_kpad(uint64_t K) { return (K + 31) / 32 * 32; }
 
 cudaError_t launch_planes(int form, const I8Consts &k, const uint64_t *op, int8_t *planes, uint64_t N, uint64_t K,
                           uint64_t Kp, cudaStream_t st);
+// small-modulus CRT forms (int8 or fp16 operands): query residue planes, two-phase product
+uint64_t crt_scratch_bytes(uint32_t n_limbs, uint32_t n_mod, uint64_t N, uint64_t M);
+cudaError_t launch_crt_planes(bool f16, const I8Consts &k, const uint64_t *op, void *planes, uint64_t N, uint64_t K,
+                              uint64_t Kp, cudaStream_t st);
+cudaError_t launch_ppmm_crt(bool f16, int bn, const I8Consts &k, const uint64_t *A, const void *Bp, uint64_t *C,
+                            uint64_t M, uint64_t N, uint64_t K, uint64_t Kp, void *scratch, cudaStream_t st);
 cudaError_t launch_ppmm_i8(int form, const I8Consts &k, const uint64_t *A, const int8_t *Bp, uint64_t *C, uint64_t M,
                            uint64_t N, uint64_t K, uint64_t Kp, cudaStream_t st);
 

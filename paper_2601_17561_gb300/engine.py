@@ -129,10 +129,18 @@ class Engine:
     def scores_bytes(self, db: Db, n_eyes: int, folded: bool) -> int:
         return C.icm_scores_bytes(self.ctx, db.handle, n_eyes, folded)
 
-    def match(self, db: Db, q: Query, stream=None, out: torch.Tensor = None) -> Scores:
+    def match_workspace(self, db: Db, n_eyes: int, form) -> torch.Tensor:
+        f = C.FORMS[form] if isinstance(form, str) else form
+        n = C.icm_match_workspace_bytes(self.ctx, db.handle, n_eyes, f)
+        return _u8(n, self.device) if n else None
+
+    def match(self, db: Db, q: Query, stream=None, out: torch.Tensor = None, ws: torch.Tensor = None) -> Scores:
         nbytes = C.icm_scores_bytes(self.ctx, db.handle, q.n_eyes, 0)
         buf = out if out is not None else _u8(nbytes, self.device)
-        h = C.icm_match(self.ctx, db.handle, q.handle, buf, nbytes, stream)
+        wsb = C.icm_match_workspace_bytes(self.ctx, db.handle, q.n_eyes, q.form)
+        if wsb and ws is None:
+            ws = _u8(wsb, self.device)
+        h = C.icm_match(self.ctx, db.handle, q.handle, buf, nbytes, ws, wsb, stream)
         return Scores(h, buf, C.icm_scores_shape(h), q.n_eyes, False, db)
 
     def fold(self, s: Scores, stream=None, out: torch.Tensor = None) -> Scores:

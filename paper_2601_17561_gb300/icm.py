@@ -48,7 +48,8 @@ _SIGS = {
     "icm_query_prepare": (_i32, [_vp, _vp, _sz, _i32, _vp, _sz, _vp, ctypes.POINTER(_vp)]),
     "icm_query_destroy": (None, [_vp]),
     "icm_scores_bytes": (_i32, [_vp, _vp, _sz, _i32, ctypes.POINTER(_sz)]),
-    "icm_match": (_i32, [_vp, _vp, _vp, _vp, _sz, _vp, ctypes.POINTER(_vp)]),
+    "icm_match_workspace_bytes": (_i32, [_vp, _vp, _sz, _i32, ctypes.POINTER(_sz)]),
+    "icm_match": (_i32, [_vp, _vp, _vp, _vp, _sz, _vp, _sz, _vp, ctypes.POINTER(_vp)]),
     "icm_fold": (_i32, [_vp, _vp, _vp, _sz, _vp, ctypes.POINTER(_vp)]),
     "icm_scores_destroy": (None, [_vp]),
     "icm_scores_shape": (_i32, [_vp, ctypes.POINTER(_sz), ctypes.POINTER(_sz), ctypes.POINTER(_sz)]),
@@ -179,9 +180,16 @@ def icm_scores_bytes(ctx, db, n_eyes, folded):
     return b.value
 
 
-def icm_match(ctx, db, q, dev_out, nbytes, stream=None):
+def icm_match_workspace_bytes(ctx, db, n_eyes, form):
+    b = ctypes.c_size_t()
+    _check(lib().icm_match_workspace_bytes(ctx, db, n_eyes, form, ctypes.byref(b)), "icm_match_workspace_bytes")
+    return b.value
+
+
+def icm_match(ctx, db, q, dev_out, nbytes, dev_ws=None, ws_bytes=0, stream=None):
     h = ctypes.c_void_p()
-    _check(lib().icm_match(ctx, db, q, _ptr(dev_out), nbytes, _stream(stream), ctypes.byref(h)), "icm_match")
+    _check(lib().icm_match(ctx, db, q, _ptr(dev_out), nbytes, _ptr(dev_ws), ws_bytes, _stream(stream), ctypes.byref(h)),
+           "icm_match")
     return h
 
 

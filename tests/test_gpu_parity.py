@@ -81,9 +81,9 @@ def test_ccmm_bit_exact(tiny, gpu_run):
     assert np.array_equal(got, tiny["C"])
 
 
-@pytest.mark.parametrize("form", ["i8_digits", "i8_crt"])
+@pytest.mark.parametrize("form", ["i8_digits", "i8_crt", "f16_crt"])
 def test_ccmm_tensor_forms_bit_exact(tiny, gpu_run, form):
-    """The int8 tensor-core forms give the same residues as the oracle (and the u64 form)."""
+    """The tensor-core forms give the same residues as the oracle (and the u64 form)."""
     eng, W = gpu_run["eng"], tiny["W"]
     q = eng.prepare(gpu_run["ct"], W.q_codes.shape[0], form)
     s = eng.match(gpu_run["db"], q)
@@ -140,7 +140,7 @@ def _rand_res(rng, q, shape):
                      for q_l in q])
 
 
-FORMS = ["u64", "i8_digits", "i8_crt"]
+FORMS = ["u64", "i8_digits", "i8_crt", "f16_crt"]
 
 
 @pytest.mark.parametrize("form", FORMS)
