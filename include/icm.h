@@ -179,6 +179,79 @@ icm_status icm_scores_shape(const icm_scores *s, size_t *n_limbs, size_t *n_cols
  * decryption is outside this library. */
 icm_status icm_decrypt_scores(icm_ctx *ctx, const icm_scores *s, int64_t *dev_num, size_t n, void *stream);
 
+/* ---------------------------------------------------------------- batching form ---- */
+
+/* Workspace bytes of icm_match_batch (the CRT forms' residue scratch over all chunks). */
+icm_status icm_match_batch_workspace_bytes(const icm_ctx *ctx, const icm_db *const *dbs, size_t n_dbs, size_t n_eyes,
+                                           icm_form form, size_t *bytes);
+
+/* CCMM of one prepared query batch against 1..16 database chunks (each its own MSRLWE database
+ * with its own a-part, uneven sizes allowed; Section 6.2.3 distributes the database the same way
+ * over GPUs).  For the CRT forms every limb, chunk, row tile, modulus and column tile of a round of
+ * up to 512 columns is one persistent kernel launch; the u64 and digit forms launch per chunk.
+ * dev_outs[i]: scores of chunk i (icm_scores_bytes of that chunk); outs[i] receives its handle. */
+icm_status icm_match_batch(icm_ctx *ctx, const icm_db *const *dbs, size_t n_dbs, const icm_query *q,
+                           void *const *dev_outs, const size_t *out_bytes, void *dev_ws, size_t ws_bytes, void *stream,
+                           icm_scores **outs);
+
+/* A captured CUDA graph of one whole batch pass on fixed buffers: query preparation from dev_ct,
+ * icm_match_batch over the chunks, and the fold of every chunk into dev_folded[i].  Created by
+ * stream capture on `stream` (which must not be the legacy default stream); replayed with
+ * icm_plan_launch on any stream.  The buffers must stay valid while the plan is used. */
+typedef struct icm_plan icm_plan;
+icm_status icm_plan_create(icm_ctx *ctx, const icm_db *const *dbs, size_t n_dbs, size_t n_eyes, icm_form form,
+                           const void *dev_ct, void *dev_op, size_t op_bytes, void *const *dev_scores,
+                           const size_t *scores_bytes, void *const *dev_folded, const size_t *folded_bytes,
+                           void *dev_ws, size_t ws_bytes, void *stream, icm_plan **out);
+icm_status icm_plan_launch(icm_plan *plan, void *stream);
+void icm_plan_destroy(icm_plan *plan);
+
+/* Autotuner: times every column-tile variant of the CRT product kernel on the caller's batch
+ * (one icm_match_batch per variant, CUDA events on `stream`), keeps the fastest for the context
+ * and reports it (0 for forms with a single variant).  ms_per_choice (optional) receives the
+ * time of each variant (128 then 256 columns). */
+icm_status icm_autotune(icm_ctx *ctx, const icm_db *const *dbs, size_t n_dbs, const icm_query *q,
+                        void *const *dev_outs, const size_t *out_bytes, void *dev_ws, size_t ws_bytes, void *stream,
+                        int *best_tile_n, float *ms_per_choice, size_t n_choices);
+
+/* ---------------------------------------------------------------- serving form ---- */
+
+/* A request loop over a resident encrypted database (Section 5: computing servers batch up to 32
+ * query eyes).  Query eyes are submitted one at a time with their wire ciphertext; a worker
+ * thread batches them (a batch starts when it holds max_eyes eyes or its oldest eye has waited
+ * window_us; eyes arriving while a batch runs join the next one), runs query preparation, the
+ * grouped CCMM and the folds, and returns every eye's folded scores.  Two I/O slots let one
+ * batch's copies overlap another's compute.  Admission: at most max_pending eyes wait (submit
+ * returns ICM_ENOMEM beyond that); a batch is admitted when an I/O slot is free. */
+typedef struct icm_server icm_server;
+typedef struct {
+    uint32_t max_eyes;       /* eyes per batch, 1..32                                          */
+    uint32_t window_us;      /* batching window for a partial batch                            */
+    icm_form form;           /* arithmetic form of the CCMM                                    */
+    uint32_t max_pending;    /* admission bound on waiting eyes (0 = 4096)                     */
+} icm_server_cfg;
+
+/* Device workspace bytes of a server (compute buffers and two I/O slots). */
+icm_status icm_server_device_bytes(const icm_ctx *ctx, const icm_db *const *dbs, size_t n_dbs,
+                                   const icm_server_cfg *cfg, size_t *bytes);
+/* Start a server on 1..16 resident chunks; dev_ws stays owned by the caller and must outlive it. */
+icm_status icm_server_create(icm_ctx *ctx, const icm_db *const *dbs, size_t n_dbs, const icm_server_cfg *cfg,
+                             void *dev_ws, size_t ws_bytes, icm_server **out);
+/* Words (u64) of one eye's ciphertext ([L_q][rho][K], the eye's columns of the wire format) and
+ * of one eye's result (for every chunk in order: [L][ceil(rho/fold_k)][M_c] folded scores). */
+icm_status icm_server_eye_words(const icm_server *s, size_t *ct_words, size_t *out_words);
+/* Queue one eye; host_ct and host_out must stay valid until icm_server_wait returns for the
+ * ticket. */
+icm_status icm_server_submit(icm_server *s, const uint64_t *host_ct, uint64_t *host_out, uint64_t *ticket);
+/* Wait (bounded) for a ticket; on success its result is in host_out and latency_ms (optional)
+ * gets the time from submission to completion.  The ticket is released. */
+icm_status icm_server_wait(icm_server *s, uint64_t ticket, uint32_t timeout_ms, double *latency_ms);
+/* Completed eyes, launched batches, and mean eyes per batch. */
+icm_status icm_server_stats(icm_server *s, uint64_t *n_done, uint64_t *n_batches, double *mean_batch);
+/* Stop accepting eyes, drain queued and running batches (bounded by timeout_ms), free the server.
+ * On ICM_ETIMEOUT the worker keeps draining in the background and the server is not freed. */
+icm_status icm_server_destroy(icm_server *s, uint32_t timeout_ms);
+
 /* ---------------------------------------------------------------- host-buffer pipeline ---- */
 
 /* Device workspace bytes of icm_match_host for n_eyes eyes of one chunk in a form. */

@@ -90,6 +90,7 @@ static long double lse2(long double a, long double b) {
 }
 
 static icm_status fail(icm_status s, const std::string &msg) { set_error(msg); return s; }
+icm_status api_fail(icm_status s, const char *msg) { set_error(msg); return s; }
 
 #define CUDA_TRY(expr)                                                                 \
     do {                                                                               \
@@ -264,6 +265,9 @@ icm_status icm_keygen(icm_ctx *c) {
     c->d_sdb_pos = a; c->d_sdb_sgn = x; c->d_sq_pos = b; c->d_sq_sgn = y;
     c->max_db_blocks = max_blocks;
     c->have_keys = true;
+    // shared-memory opt-ins of the product kernels are set once here, outside any stream capture
+    e = crt_set_attributes();
+    if (e != cudaSuccess) return fail(ICM_ECUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));
     return ICM_OK;
 }
 
@@ -547,6 +551,7 @@ icm_status icm_ppmm(icm_form form, const uint64_t *q, uint32_t n_limbs, const ui
     if (3 * (uint64_t)K >= (1ull << 24)) return fail(ICM_EBOUND, "K too large for exact accumulation");
     std::vector<uint64_t> qv(q, q + n_limbs);
     const LimbTable lt = make_limb_table(qv);
+    if (crt_set_attributes() != cudaSuccess) return fail(ICM_ECUDA, "kernel attributes");
     cudaError_t e;
     switch (form) {
         case ICM_FORM_U64: e = launch_ppmm_u64(lt, dev_A, dev_B, dev_C, M, N, K, (cudaStream_t)stream); break;

@@ -36,11 +36,12 @@ constexpr int BM = 128, KS = 32, NT = 256, FLUSH = 512;
 constexpr uint64_t NCHUNK = 512;            // columns per phase-1/phase-2 round
 
 struct P1Args {
-    const uint64_t *A;       // [L][M][K]
+    icm::ChunkTab tab;       // database chunks: A_c [L][M_c][K], scratch row offsets, row-tile offsets
     const void *Bp;          // [L][r][N][Kp] int8 or fp16 planes
-    uint8_t *R;              // [L][r][nch][M] scratch
-    uint64_t M, N, K, Kp, n0, nch;
+    uint8_t *R;              // [L][r][nch][sum M_c] scratch
+    uint64_t N, K, Kp, n0, nch;
     uint32_t n_ntile;
+    uint64_t n_tiles;        // L * (row tiles of all chunks) * r * n_ntile
     icm::I8Consts k;
 };
 
@@ -111,19 +112,29 @@ __global__ void __launch_bounds__(NT, 1) k_crt_p1(P1Args p) {
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned char *sA = smem;                                   // [2][BM][LDB]
     unsigned char *sB = smem + 2 * BM * LDB;                    // [2][BN][LDB]
-
-    const uint32_t nt = blockIdx.x % p.n_ntile, mi = blockIdx.x / p.n_ntile;
-    const uint32_t l = blockIdx.z;
-    const uint64_t m0 = (uint64_t)blockIdx.y * BM, nb = (uint64_t)nt * BN;   // nb: column within the chunk
-    const uint64_t M = p.M, N = p.N, K = p.K, Kp = p.Kp;
     const uint32_t r = p.k.n_mod;
+    const uint32_t mt_total = p.tab.mt0[p.tab.n];
+    const uint64_t N = p.N, K = p.K, Kp = p.Kp;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp & 1, wn = warp >> 1;
+
+    // persistent loop: tiles ordered (limb, row tile, modulus, column tile), column tile fastest,
+    // so that the blocks running at the same time share database slabs through L2
+    for (uint64_t tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x) {
+    uint64_t tt = tile;
+    const uint32_t nt = (uint32_t)(tt % p.n_ntile); tt /= p.n_ntile;
+    const uint32_t mi = (uint32_t)(tt % r); tt /= r;
+    const uint32_t mtg = (uint32_t)(tt % mt_total);
+    const uint32_t l = (uint32_t)(tt / mt_total);
+    uint32_t c = 0;
+    while (c + 1 < p.tab.n && mtg >= p.tab.mt0[c + 1]) ++c;
+    const uint64_t M = p.tab.M[c];
+    const uint64_t m0 = (uint64_t)(mtg - p.tab.mt0[c]) * BM, nb = (uint64_t)nt * BN;   // nb: column within the chunk
     const int m = p.k.mod[mi], wlo = p.k.wlo[mi], whi = p.k.whi[mi];
     const float inv_m = p.k.inv_m[mi];
     const uint64_t q = p.k.q[l];
-    const uint64_t *Al = p.A + (size_t)l * M * K;
+    const uint64_t *Al = p.tab.A[c] + (size_t)l * M * K;
     const unsigned char *Bl = reinterpret_cast<const unsigned char *>(p.Bp) + (((size_t)l * r + mi) * N + p.n0) * Kp * ESZ;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = warp & 1, wn = warp >> 1;
 
     AccT acc[4][NT8][4];
 #pragma unroll
@@ -131,7 +142,7 @@ __global__ void __launch_bounds__(NT, 1) k_crt_p1(P1Args p) {
 #pragma unroll
         for (int b = 0; b < NT8; ++b)
 #pragma unroll
-            for (int c = 0; c < 4; ++c) acc[a][b][c] = 0;
+            for (int cc = 0; cc < 4; ++cc) acc[a][b][cc] = 0;
 
     uint64_t ra[4][4];                            // prefetched slab: 4 groups of 4 consecutive k
     auto load_a = [&](uint64_t k0) {
@@ -210,8 +221,8 @@ __global__ void __launch_bounds__(NT, 1) k_crt_p1(P1Args p) {
 #pragma unroll
                 for (int b = 0; b < NT8; ++b)
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        float &x = reinterpret_cast<float &>(acc[a][b][c]);
+                    for (int cc = 0; cc < 4; ++cc) {
+                        float &x = reinterpret_cast<float &>(acc[a][b][cc]);
                         x = fmaf(-fm, rintf(x * inv_m), x);
                     }
         }
@@ -220,38 +231,46 @@ __global__ void __launch_bounds__(NT, 1) k_crt_p1(P1Args p) {
         __syncthreads();
     }
 
-    // c_i in [0, m) to the scratch, column-major within the chunk
+    // c_i in [0, m) to the scratch, column-major within the column chunk, rows of all chunks
     const int g = lane >> 2, tq = lane & 3;
-    uint8_t *Rl = p.R + ((size_t)l * r + mi) * p.nch * M;
+    const uint64_t Mall = p.tab.row0[p.tab.n];
+    uint8_t *Rl = p.R + ((size_t)l * r + mi) * p.nch * Mall + p.tab.row0[c];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < NT8; ++b)
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const uint64_t row = m0 + wm * 64 + a * 16 + g + (c >> 1) * 8;
-                const uint64_t col = nb + wn * WN + b * 8 + tq * 2 + (c & 1);
+            for (int cc = 0; cc < 4; ++cc) {
+                const uint64_t row = m0 + wm * 64 + a * 16 + g + (cc >> 1) * 8;
+                const uint64_t col = nb + wn * WN + b * 8 + tq * 2 + (cc & 1);
                 if (row >= M || col >= p.nch || p.n0 + col >= N) continue;
                 int v;
-                if (F16) v = __float2int_rn(reinterpret_cast<const float &>(acc[a][b][c])) % m;
-                else v = reinterpret_cast<const int &>(acc[a][b][c]) % m;
+                if (F16) v = __float2int_rn(reinterpret_cast<const float &>(acc[a][b][cc])) % m;
+                else v = reinterpret_cast<const int &>(acc[a][b][cc]) % m;
                 v = v < 0 ? v + m : v;
-                Rl[col * M + row] = (uint8_t)v;
+                Rl[col * Mall + row] = (uint8_t)v;
             }
+    __syncthreads();          // shared buffers are reused by the next tile
+    }
 }
 
 struct P2Args {
-    const uint8_t *R;        // [L][r][nch][M]
-    uint64_t *C;             // [L][N][M]
-    uint64_t M, N, n0, nch;
+    icm::ChunkTab tab;       // outputs C_c [L][N][M_c]
+    const uint8_t *R;        // [L][r][nch][sum M_c]
+    uint64_t N, n0, nch;
     icm::I8Consts k;
 };
 
 __global__ void __launch_bounds__(256) k_crt_combine(P2Args p) {
-    const uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;   // within the chunk
+    const uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;   // (column, row) within the round
     const uint32_t l = blockIdx.y;
-    const uint64_t cnt = p.nch * p.M;
+    const uint64_t Mall = p.tab.row0[p.tab.n];
+    const uint64_t cnt = p.nch * Mall;
     if (idx >= cnt) return;
+    const uint64_t col = idx / Mall, grow = idx % Mall;
+    uint32_t c = 0;
+    while (c + 1 < p.tab.n && grow >= p.tab.row0[c + 1]) ++c;
+    const uint64_t row = grow - p.tab.row0[c], M = p.tab.M[c];
     const uint32_t r = p.k.n_mod;
     const uint64_t q = p.k.q[l];
     const uint8_t *Rl = p.R + (size_t)l * r * cnt + idx;
@@ -264,7 +283,7 @@ __global__ void __launch_bounds__(256) k_crt_combine(P2Args p) {
         F += (float)y * p.k.inv_m[i];
     }
     const uint64_t kappa = (uint64_t)__float2int_rn(F);
-    p.C[((size_t)l * p.N + p.n0) * p.M + idx] = sub_mod(S, mulmod_shoup(kappa, p.k.Mq[l], p.k.Mqs[l], q), q);
+    p.tab.C[c][((size_t)l * p.N + p.n0 + col) * M + row] = sub_mod(S, mulmod_shoup(kappa, p.k.Mq[l], p.k.Mqs[l], q), q);
 }
 
 // Residue planes of the query operand: [L][r][N][Kp] (int8 or fp16), zero padded.
@@ -288,13 +307,23 @@ __global__ void __launch_bounds__(256) k_crt_planes(const uint64_t *op, void *pl
 }
 
 template <bool F16, int BN>
+constexpr size_t p1_smem() { return (size_t)2 * (BM + BN) * (KS * (F16 ? 2 : 1) + 16); }
+
+template <bool F16, int BN>
+cudaError_t set_p1_attr() {
+    return cudaFuncSetAttribute(k_crt_p1<F16, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p1_smem<F16, BN>());
+}
+
+template <bool F16, int BN>
 cudaError_t run_p1(const P1Args &a, cudaStream_t st) {
-    constexpr int LDB = KS * (F16 ? 2 : 1) + 16;
-    const size_t smem = (size_t)2 * (BM + BN) * LDB;
-    cudaError_t e = cudaFuncSetAttribute(k_crt_p1<F16, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    dim3 grid(a.n_ntile * a.k.n_mod, (unsigned)((a.M + BM - 1) / BM), a.k.n_limbs);
-    k_crt_p1<F16, BN><<<grid, NT, smem, st>>>(a);
+    const size_t smem = p1_smem<F16, BN>();
+    cudaError_t e;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const uint64_t grid = std::min<uint64_t>(a.n_tiles, (uint64_t)sms);     // one resident block per SM
+    if (grid == 0) return cudaSuccess;
+    k_crt_p1<F16, BN><<<(unsigned)grid, NT, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -302,8 +331,32 @@ cudaError_t run_p1(const P1Args &a, cudaStream_t st) {
 
 namespace icm {
 
+cudaError_t crt_set_attributes() {
+    cudaError_t e = set_p1_attr<true, 128>();
+    if (e == cudaSuccess) e = set_p1_attr<true, 256>();
+    if (e == cudaSuccess) e = set_p1_attr<false, 128>();
+    if (e == cudaSuccess) e = set_p1_attr<false, 256>();
+    return e;
+}
+
 uint64_t crt_scratch_bytes(uint32_t n_limbs, uint32_t n_mod, uint64_t N, uint64_t M) {
     return (uint64_t)n_limbs * n_mod * std::min<uint64_t>(N, NCHUNK) * M;
+}
+
+bool make_chunk_tab(const uint64_t *const *A, uint64_t *const *C, const uint64_t *M, uint32_t n, ChunkTab &t) {
+    if (n == 0 || n > ICM_MAX_CHUNKS) return false;
+    t = ChunkTab{};
+    t.n = n;
+    t.row0[0] = 0;
+    t.mt0[0] = 0;
+    for (uint32_t c = 0; c < n; ++c) {
+        t.A[c] = A[c];
+        t.C[c] = C[c];
+        t.M[c] = M[c];
+        t.row0[c + 1] = t.row0[c] + M[c];
+        t.mt0[c + 1] = t.mt0[c] + (uint32_t)((M[c] + BM - 1) / BM);
+    }
+    return true;
 }
 
 cudaError_t launch_crt_planes(bool f16, const I8Consts &k, const uint64_t *op, void *planes, uint64_t N, uint64_t K,
@@ -316,23 +369,35 @@ cudaError_t launch_crt_planes(bool f16, const I8Consts &k, const uint64_t *op, v
     return cudaGetLastError();
 }
 
-cudaError_t launch_ppmm_crt(bool f16, int bn, const I8Consts &k, const uint64_t *A, const void *Bp, uint64_t *C,
-                            uint64_t M, uint64_t N, uint64_t K, uint64_t Kp, void *scratch, cudaStream_t st) {
-    if (M == 0 || N == 0) return cudaSuccess;
+cudaError_t launch_ppmm_crt_grouped(bool f16, int bn, const I8Consts &k, const ChunkTab &tab, const void *Bp, uint64_t N,
+                                    uint64_t K, uint64_t Kp, void *scratch, cudaStream_t st) {
+    const uint64_t Mall = tab.row0[tab.n];
+    if (Mall == 0 || N == 0) return cudaSuccess;
     for (uint64_t n0 = 0; n0 < N; n0 += NCHUNK) {
         const uint64_t nch = std::min<uint64_t>(NCHUNK, N - n0);
-        P1Args a{A, Bp, reinterpret_cast<uint8_t *>(scratch), M, N, K, Kp, n0, nch,
-                 (uint32_t)((nch + bn - 1) / bn), k};
+        P1Args a{};
+        a.tab = tab; a.Bp = Bp; a.R = reinterpret_cast<uint8_t *>(scratch);
+        a.N = N; a.K = K; a.Kp = Kp; a.n0 = n0; a.nch = nch;
+        a.n_ntile = (uint32_t)((nch + bn - 1) / bn);
+        a.n_tiles = (uint64_t)k.n_limbs * tab.mt0[tab.n] * k.n_mod * a.n_ntile;
+        a.k = k;
         cudaError_t e;
         if (f16) e = bn == 128 ? run_p1<true, 128>(a, st) : run_p1<true, 256>(a, st);
         else e = bn == 128 ? run_p1<false, 128>(a, st) : run_p1<false, 256>(a, st);
         if (e != cudaSuccess) return e;
-        P2Args b{reinterpret_cast<const uint8_t *>(scratch), C, M, N, n0, nch, k};
-        k_crt_combine<<<dim3((unsigned)((nch * M + 255) / 256), k.n_limbs), 256, 0, st>>>(b);
+        P2Args b{tab, reinterpret_cast<const uint8_t *>(scratch), N, n0, nch, k};
+        k_crt_combine<<<dim3((unsigned)((nch * Mall + 255) / 256), k.n_limbs), 256, 0, st>>>(b);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+cudaError_t launch_ppmm_crt(bool f16, int bn, const I8Consts &k, const uint64_t *A, const void *Bp, uint64_t *C,
+                            uint64_t M, uint64_t N, uint64_t K, uint64_t Kp, void *scratch, cudaStream_t st) {
+    ChunkTab tab;
+    make_chunk_tab(&A, &C, &M, 1, tab);
+    return launch_ppmm_crt_grouped(f16, bn, k, tab, Bp, N, K, Kp, scratch, st);
 }
 
 }  // namespace icm

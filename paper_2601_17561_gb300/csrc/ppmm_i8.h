@@ -32,6 +32,20 @@ inline uint64_t i8_kpad(uint64_t K) { return (K + 31) / 32 * 32; }
 
 cudaError_t launch_planes(int form, const I8Consts &k, const uint64_t *op, int8_t *planes, uint64_t N, uint64_t K,
                           uint64_t Kp, cudaStream_t st);
+#define ICM_MAX_CHUNKS 16
+// Database chunks of one grouped launch.
+struct ChunkTab {
+    uint32_t n;
+    const uint64_t *A[ICM_MAX_CHUNKS];     // [L][M_c][K]
+    uint64_t *C[ICM_MAX_CHUNKS];           // [L][N][M_c]
+    uint64_t M[ICM_MAX_CHUNKS];
+    uint64_t row0[ICM_MAX_CHUNKS + 1];     // prefix sums of M_c
+    uint32_t mt0[ICM_MAX_CHUNKS + 1];      // prefix sums of 128-row tiles
+};
+bool make_chunk_tab(const uint64_t *const *A, uint64_t *const *C, const uint64_t *M, uint32_t n, ChunkTab &t);
+cudaError_t launch_ppmm_crt_grouped(bool f16, int bn, const I8Consts &k, const ChunkTab &tab, const void *Bp, uint64_t N,
+                                    uint64_t K, uint64_t Kp, void *scratch, cudaStream_t st);
+cudaError_t crt_set_attributes();
 // small-modulus CRT forms (int8 or fp16 operands): query residue planes, two-phase product
 uint64_t crt_scratch_bytes(uint32_t n_limbs, uint32_t n_mod, uint64_t N, uint64_t M);
 cudaError_t launch_crt_planes(bool f16, const I8Consts &k, const uint64_t *op, void *planes, uint64_t N, uint64_t K,

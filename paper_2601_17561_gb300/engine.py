@@ -149,11 +149,107 @@ class Engine:
         h = C.icm_fold(self.ctx, s.handle, buf, nbytes, stream)
         return Scores(h, buf, C.icm_scores_shape(h), s.n_eyes, True, s.db)
 
+    # -------------------------------------------------------------------- batching form
+    def match_batch(self, dbs, q: Query, stream=None, outs=None, ws: torch.Tensor = None):
+        """CCMM of one query batch against several database chunks in one grouped launch."""
+        sizes = [C.icm_scores_bytes(self.ctx, d.handle, q.n_eyes, 0) for d in dbs]
+        outs = outs if outs is not None else [_u8(n, self.device) for n in sizes]
+        wsb = C.icm_match_batch_workspace_bytes(self.ctx, [d.handle for d in dbs], q.n_eyes, q.form)
+        if wsb and ws is None:
+            ws = _u8(wsb, self.device)
+        hs = C.icm_match_batch(self.ctx, [d.handle for d in dbs], q.handle, outs, sizes, ws, wsb, stream)
+        return [Scores(h, b, C.icm_scores_shape(h), q.n_eyes, False, d) for h, b, d in zip(hs, outs, dbs)]
+
+    def autotune(self, dbs, q: Query, stream=None):
+        sizes = [C.icm_scores_bytes(self.ctx, d.handle, q.n_eyes, 0) for d in dbs]
+        outs = [_u8(n, self.device) for n in sizes]
+        wsb = C.icm_match_batch_workspace_bytes(self.ctx, [d.handle for d in dbs], q.n_eyes, q.form)
+        ws = _u8(wsb, self.device) if wsb else None
+        return C.icm_autotune(self.ctx, [d.handle for d in dbs], q.handle, outs, sizes, ws, wsb, stream)
+
+    def plan(self, dbs, n_eyes: int, form, ct: torch.Tensor, stream):
+        """Capture prepare + grouped CCMM + folds on fixed buffers into a CUDA graph."""
+        return Plan(self, dbs, n_eyes, form, ct, stream)
+
     def decrypt(self, s: Scores, stream=None) -> torch.Tensor:
         n = s.shape[1] * s.db.n_real
         out = torch.empty(max(n, 1), dtype=torch.int64, device=self.device)
         C.icm_decrypt_scores(self.ctx, s.handle, out, n, stream)
         return out[:n].view(s.shape[1], s.db.n_real)
+
+
+class Plan:
+    """A CUDA graph of one batch pass (query preparation, grouped CCMM, folds) on fixed buffers."""
+
+    def __init__(self, eng: Engine, dbs, n_eyes: int, form, ct: torch.Tensor, stream):
+        f = C.FORMS[form] if isinstance(form, str) else form
+        self.eng, self.dbs, self.n_eyes, self.form, self.ct = eng, dbs, n_eyes, f, ct
+        dev = eng.device
+        self.op_bytes = C.icm_query_op_bytes(eng.ctx, n_eyes, f)
+        self.op = _u8(self.op_bytes, dev)
+        self.sc_bytes = [C.icm_scores_bytes(eng.ctx, d.handle, n_eyes, 0) for d in dbs]
+        self.fo_bytes = [C.icm_scores_bytes(eng.ctx, d.handle, n_eyes, 1) for d in dbs]
+        self.scores = [_u8(n, dev) for n in self.sc_bytes]
+        self.folded = [_u8(n, dev) for n in self.fo_bytes]
+        self.ws_bytes = C.icm_match_batch_workspace_bytes(eng.ctx, [d.handle for d in dbs], n_eyes, f)
+        self.ws = _u8(self.ws_bytes, dev) if self.ws_bytes else None
+        self.handle = C.icm_plan_create(eng.ctx, [d.handle for d in dbs], n_eyes, f, ct, self.op, self.op_bytes,
+                                        self.scores, self.sc_bytes, self.folded, self.fo_bytes, self.ws, self.ws_bytes,
+                                        stream)
+
+    def launch(self, stream=None):
+        C.icm_plan_launch(self.handle, stream)
+
+    def folded_residues(self, i: int) -> np.ndarray:
+        L = self.eng.L
+        groups = (self.eng.rho + self.eng.fold_k - 1) // self.eng.fold_k
+        M = self.dbs[i].m_rows
+        n = L * self.n_eyes * groups * M
+        return self.folded[i][: n * 8].view(torch.int64).cpu().numpy().view(np.uint64).reshape(L, self.n_eyes * groups, M)
+
+    def __del__(self):
+        if getattr(self, "handle", None) is not None:
+            C.icm_plan_destroy(self.handle)
+            self.handle = None
+
+
+class Server:
+    """Serving loop over resident chunks (icm_server_*): submit one eye at a time, wait per ticket."""
+
+    def __init__(self, eng: Engine, dbs, form="f16_crt", max_eyes=32, window_us=2000, max_pending=0):
+        f = C.FORMS[form] if isinstance(form, str) else form
+        self.eng, self.dbs = eng, dbs
+        cfg = C.icm_server_cfg(max_eyes=max_eyes, window_us=window_us, form=f, max_pending=max_pending)
+        nbytes = C.icm_server_device_bytes(eng.ctx, [d.handle for d in dbs], cfg)
+        self.ws = _u8(nbytes, eng.device)
+        torch.cuda.synchronize()
+        self.handle = C.icm_server_create(eng.ctx, [d.handle for d in dbs], cfg, self.ws, nbytes)
+        self.ct_words, self.out_words = C.icm_server_eye_words(self.handle)
+
+    def eye_cts(self, ct: torch.Tensor, n_eyes: int) -> list:
+        """Split a device wire ciphertext of n_eyes eyes into per-eye host arrays [Lq][rho][K]."""
+        Lq = self.ct_words // (self.eng.rho * self.eng.K)
+        full = ct[: Lq * n_eyes * self.eng.rho * self.eng.K * 8].view(torch.int64).cpu().numpy().view(np.uint64)
+        full = full.reshape(Lq, n_eyes, self.eng.rho, self.eng.K)
+        return [np.ascontiguousarray(full[:, e]) for e in range(n_eyes)]
+
+    def submit(self, ct_eye: np.ndarray, out: np.ndarray) -> int:
+        assert ct_eye.size == self.ct_words and out.size == self.out_words
+        return C.icm_server_submit(self.handle, ct_eye, out)
+
+    def wait(self, ticket: int, timeout_ms: int = 600000) -> float:
+        return C.icm_server_wait(self.handle, ticket, timeout_ms)
+
+    def stats(self):
+        return C.icm_server_stats(self.handle)
+
+    def close(self, timeout_ms: int = 600000):
+        if self.handle is not None:
+            C.icm_server_destroy(self.handle, timeout_ms)
+            self.handle = None
+
+    def __del__(self):
+        self.close()
 
 
 def ppmm(form, q, A: torch.Tensor, B: torch.Tensor, stream=None) -> torch.Tensor:

@@ -23,6 +23,11 @@ class IcmError(RuntimeError):
         super().__init__(f"{where}: status {status} ({detail})")
 
 
+class icm_server_cfg(ctypes.Structure):
+    _fields_ = [("max_eyes", ctypes.c_uint32), ("window_us", ctypes.c_uint32), ("form", ctypes.c_int),
+                ("max_pending", ctypes.c_uint32)]
+
+
 class icm_params(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint32) for n in (
         "log_n_db", "log_n_q", "n_limbs", "n_limbs_q", "prime_bits", "code_bits", "d2", "rho", "fold_k",
@@ -60,6 +65,21 @@ _SIGS = {
     "icm_match_host_workspace_bytes": (_i32, [_vp, _vp, _sz, _i32, ctypes.POINTER(_sz)]),
     "icm_match_host": (_i32, [_vp, _vp, _vp, _sz, _i32, _vp, _vp, _sz, _vp]),
     "icm_probe_peak": (_i32, [_i32, ctypes.POINTER(ctypes.c_double), _vp]),
+    "icm_match_batch_workspace_bytes": (_i32, [_vp, _vp, _sz, _sz, _i32, ctypes.POINTER(_sz)]),
+    "icm_match_batch": (_i32, [_vp, _vp, _sz, _vp, _vp, _vp, _vp, _sz, _vp, _vp]),
+    "icm_plan_create": (_i32, [_vp, _vp, _sz, _sz, _i32, _vp, _vp, _sz, _vp, _vp, _vp, _vp, _vp, _sz, _vp,
+                               ctypes.POINTER(_vp)]),
+    "icm_plan_launch": (_i32, [_vp, _vp]),
+    "icm_plan_destroy": (None, [_vp]),
+    "icm_server_device_bytes": (_i32, [_vp, _vp, _sz, _vp, ctypes.POINTER(_sz)]),
+    "icm_server_create": (_i32, [_vp, _vp, _sz, _vp, _vp, _sz, ctypes.POINTER(_vp)]),
+    "icm_server_eye_words": (_i32, [_vp, ctypes.POINTER(_sz), ctypes.POINTER(_sz)]),
+    "icm_server_submit": (_i32, [_vp, _vp, _vp, ctypes.POINTER(_u64)]),
+    "icm_server_wait": (_i32, [_vp, _u64, _u32, ctypes.POINTER(ctypes.c_double)]),
+    "icm_server_stats": (_i32, [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64), ctypes.POINTER(ctypes.c_double)]),
+    "icm_server_destroy": (_i32, [_vp, _u32]),
+    "icm_autotune": (_i32, [_vp, _vp, _sz, _vp, _vp, _vp, _vp, _sz, _vp, ctypes.POINTER(_i32),
+                            ctypes.POINTER(ctypes.c_float), _sz]),
 }
 
 
@@ -240,6 +260,100 @@ def icm_probe_peak(kind: int, stream=None) -> float:
     v = ctypes.c_double()
     _check(lib().icm_probe_peak(kind, ctypes.byref(v), _stream(stream)), "icm_probe_peak")
     return v.value
+
+
+def _ptr_array(xs):
+    return (ctypes.c_void_p * len(xs))(*[(_ptr(x).value if x is not None else None) for x in xs])
+
+
+def _handle_array(hs):
+    return (ctypes.c_void_p * len(hs))(*[h.value for h in hs])
+
+
+def _size_array(ns):
+    return (ctypes.c_size_t * len(ns))(*ns)
+
+
+def icm_match_batch_workspace_bytes(ctx, dbs, n_eyes, form):
+    b = ctypes.c_size_t()
+    _check(lib().icm_match_batch_workspace_bytes(ctx, _handle_array(dbs), len(dbs), n_eyes, form, ctypes.byref(b)),
+           "icm_match_batch_workspace_bytes")
+    return b.value
+
+
+def icm_match_batch(ctx, dbs, q, dev_outs, out_bytes, dev_ws, ws_bytes, stream=None):
+    outs = (ctypes.c_void_p * len(dbs))()
+    _check(lib().icm_match_batch(ctx, _handle_array(dbs), len(dbs), q, _ptr_array(dev_outs), _size_array(out_bytes),
+                                 _ptr(dev_ws), ws_bytes, _stream(stream), outs), "icm_match_batch")
+    return [ctypes.c_void_p(h) for h in outs]
+
+
+def icm_plan_create(ctx, dbs, n_eyes, form, dev_ct, dev_op, op_bytes, dev_scores, scores_bytes, dev_folded,
+                    folded_bytes, dev_ws, ws_bytes, stream):
+    h = ctypes.c_void_p()
+    _check(lib().icm_plan_create(ctx, _handle_array(dbs), len(dbs), n_eyes, form, _ptr(dev_ct), _ptr(dev_op), op_bytes,
+                                 _ptr_array(dev_scores), _size_array(scores_bytes), _ptr_array(dev_folded),
+                                 _size_array(folded_bytes), _ptr(dev_ws), ws_bytes, _stream(stream), ctypes.byref(h)),
+           "icm_plan_create")
+    return h
+
+
+def icm_plan_launch(plan, stream=None):
+    _check(lib().icm_plan_launch(plan, _stream(stream)), "icm_plan_launch")
+
+
+def icm_plan_destroy(plan):
+    lib().icm_plan_destroy(plan)
+
+
+def icm_autotune(ctx, dbs, q, dev_outs, out_bytes, dev_ws, ws_bytes, stream=None):
+    best = ctypes.c_int()
+    ms = (ctypes.c_float * 2)()
+    _check(lib().icm_autotune(ctx, _handle_array(dbs), len(dbs), q, _ptr_array(dev_outs), _size_array(out_bytes),
+                              _ptr(dev_ws), ws_bytes, _stream(stream), ctypes.byref(best), ms, 2), "icm_autotune")
+    return best.value, list(ms)
+
+
+def icm_server_device_bytes(ctx, dbs, cfg):
+    b = ctypes.c_size_t()
+    _check(lib().icm_server_device_bytes(ctx, _handle_array(dbs), len(dbs), ctypes.byref(cfg), ctypes.byref(b)),
+           "icm_server_device_bytes")
+    return b.value
+
+
+def icm_server_create(ctx, dbs, cfg, dev_ws, ws_bytes):
+    h = ctypes.c_void_p()
+    _check(lib().icm_server_create(ctx, _handle_array(dbs), len(dbs), ctypes.byref(cfg), _ptr(dev_ws), ws_bytes,
+                                   ctypes.byref(h)), "icm_server_create")
+    return h
+
+
+def icm_server_eye_words(srv):
+    a, b = ctypes.c_size_t(), ctypes.c_size_t()
+    _check(lib().icm_server_eye_words(srv, ctypes.byref(a), ctypes.byref(b)), "icm_server_eye_words")
+    return a.value, b.value
+
+
+def icm_server_submit(srv, host_ct, host_out):
+    t = ctypes.c_uint64()
+    _check(lib().icm_server_submit(srv, _ptr(host_ct), _ptr(host_out), ctypes.byref(t)), "icm_server_submit")
+    return t.value
+
+
+def icm_server_wait(srv, ticket, timeout_ms=600000):
+    lat = ctypes.c_double()
+    _check(lib().icm_server_wait(srv, ticket, timeout_ms, ctypes.byref(lat)), "icm_server_wait")
+    return lat.value
+
+
+def icm_server_stats(srv):
+    a, b, m = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_double()
+    _check(lib().icm_server_stats(srv, ctypes.byref(a), ctypes.byref(b), ctypes.byref(m)), "icm_server_stats")
+    return a.value, b.value, m.value
+
+
+def icm_server_destroy(srv, timeout_ms=600000):
+    _check(lib().icm_server_destroy(srv, timeout_ms), "icm_server_destroy")
 
 
 def icm_sync(stream=None, timeout_ms: int = 600000):

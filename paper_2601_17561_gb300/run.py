@@ -1,0 +1,53 @@
+"""Run one matching pass of a named synthetic workload through the library (CLI).
+
+    python -m paper_2601_17561_gb300.run --workload mid --form f16_crt --passes 2
+
+Workloads: tiny (4 eyes x 256 codes, ring 2^12, 3 primes < 2^50), mid (32 eyes x 2,000 codes,
+same ring and primes: about 3 GB on the device, sized for profiler captures), paper (32 eyes x
+114,688 codes, N_db = 2^14, N_q = 2^13, 8 primes < 2^60).  Each pass prepares the query,
+runs the CCMM and the fold.
+"""
+from __future__ import annotations
+
+import argparse
+import sys
+import time
+
+import torch
+
+from . import build as B
+from . import engine as E
+from . import synth
+
+WORKLOADS = {
+    "tiny": (E.TINY, dict(n_eyes=4, n_db=256, seed=1, planted_frac=0.05)),
+    "mid": (E.TINY, dict(n_eyes=32, n_db=2000, seed=3, planted_frac=0.05)),
+    "paper": (E.PAPER, dict(n_eyes=32, n_db=7 * (1 << 14), seed=2, planted_frac=0.05)),
+}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="tiny", choices=sorted(WORKLOADS))
+    ap.add_argument("--form", default="f16_crt", choices=["u64", "i8_digits", "i8_crt", "f16_crt"])
+    ap.add_argument("--passes", type=int, default=1)
+    a = ap.parse_args(argv)
+    B.build()
+    params, wl = WORKLOADS[a.workload]
+    W = synth.make_workload(**wl)
+    eng = E.Engine(**params).keygen()
+    db = eng.encrypt_db(W.db_codes, W.db_masks)
+    ct = eng.encrypt_query(W.q_codes, W.q_masks, W.eye_ids)
+    torch.cuda.synchronize()
+    for i in range(a.passes):
+        t0 = time.perf_counter()
+        q = eng.prepare(ct, wl["n_eyes"], a.form)
+        s = eng.match(db, q)
+        eng.fold(s)
+        torch.cuda.synchronize()
+        print(f"pass {i}: {(time.perf_counter() - t0) * 1e3:.1f} ms ({a.workload}, {a.form})", flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
