@@ -176,6 +176,7 @@ def main():
     ap.add_argument("--compare-forms", default="i8_crt,u64,i8_digits",
                     help="comma list of other forms, each timed for one step on the same workload ('' to skip)")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--variant", default="auto", help="CRT product kernel: auto (autotuner), 0, 1 (tcgen05) or 128")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     ws, rank, local = _dist()
@@ -211,6 +212,18 @@ def main():
     torch.cuda.synchronize()
     st = torch.cuda.Stream(device=dev)
     comps = N_EYES * N_DB
+
+    # kernel variant of the CRT forms: autotuned on this workload (untimed) or fixed
+    tune = None
+    if args.form in ("i8_crt", "f16_crt"):
+        if args.variant == "auto":
+            qt = eng.prepare(ct, N_EYES, args.form)
+            best, ms = eng.autotune([db], qt)
+            tune = {"chosen": best, "ms": dict(zip(["mma.sync-128", "mma.sync-256", "tcgen05"], ms))}
+            del qt
+        else:
+            C.icm_ctx_set_variant(eng.ctx, int(args.variant))
+            tune = {"chosen": int(args.variant)}
 
     def timed_form(form: str, steps: int, warmup: int):
         """warmup (>= 1) untimed steps, barrier, then `steps` steps timed with CUDA events on the
@@ -334,7 +347,7 @@ def main():
                        "l2": "inputs larger than L2 (206 GB resident database), no flush",
                        "parallelism": "replicas" if ws == 1 else f"weak: {ws} database shards, same query"},
             "roofline": roof, "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clk,
-            "forms": forms}
+            "forms": forms, "variant": tune}
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         v, thr, sample, _ = oracle_sample(seconds_target=15.0)

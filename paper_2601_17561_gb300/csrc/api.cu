@@ -191,8 +191,8 @@ icm_status icm_ctx_create(const icm_params *p, icm_ctx **out) {
     }
     {
         const char *why = nullptr;
-        make_i8_consts(ICM_FORM_I8_DIGITS, q, K, c->i8_digits, &why);
-        c->i8_crt_ok = make_i8_consts(ICM_FORM_I8_CRT, q, K, c->i8_crt, &why);
+        make_i8_consts(ICM_FORM_I8_DIGITS, q.data(), q.size(), K, c->i8_digits, &why);
+        c->i8_crt_ok = make_i8_consts(ICM_FORM_I8_CRT, q.data(), q.size(), K, c->i8_crt, &why);
     }
     long double qod = 1;
     for (uint32_t l = 0; l < P.n_limbs_q; ++l) qod *= (long double)q[l];
@@ -414,19 +414,19 @@ icm_status icm_match(icm_ctx *c, const icm_db *db, const icm_query *q, void *dev
     switch (q->form) {
         case ICM_FORM_U64:
             e = launch_ppmm_u64(c->lt, db->dev, (const uint64_t *)q->dev, (uint64_t *)dev_out, db->lay.M, q->n_cols, c->K,
-                                (cudaStream_t)stream);
+                                true, (cudaStream_t)stream);
             break;
         case ICM_FORM_I8_DIGITS: {
             const int8_t *planes = (const int8_t *)q->dev + (size_t)c->p.n_limbs * q->n_cols * c->K * 8;
-            e = launch_ppmm_i8(q->form, c->i8_digits, db->dev, planes, (uint64_t *)dev_out, db->lay.M, q->n_cols, c->K,
-                               i8_kpad(c->K), (cudaStream_t)stream);
+            e = launch_ppmm_i8(q->form, c->i8_digits, db->dev, true, planes, (uint64_t *)dev_out, db->lay.M, q->n_cols,
+                               c->K, i8_kpad(c->K), (cudaStream_t)stream);
             break;
         }
         case ICM_FORM_I8_CRT:
         case ICM_FORM_F16_CRT: {
             const void *planes = (const char *)q->dev + (size_t)c->p.n_limbs * q->n_cols * c->K * 8;
-            e = launch_ppmm_crt(q->form == ICM_FORM_F16_CRT, c->crt_bn, c->i8_crt, db->dev, planes, (uint64_t *)dev_out,
-                                db->lay.M, q->n_cols, c->K, i8_kpad(c->K), dev_ws, (cudaStream_t)stream);
+            e = launch_ppmm_crt(q->form == ICM_FORM_F16_CRT, c->crt_bn, c->i8_crt, db->dev, true, planes,
+                                (uint64_t *)dev_out, db->lay.M, q->n_cols, c->K, i8_kpad(c->K), dev_ws, (cudaStream_t)stream);
             break;
         }
         default: delete sc; return fail(ICM_EUNSUPPORTED, "form not built");
@@ -530,7 +530,8 @@ icm_status icm_ppmm_workspace_bytes(icm_form form, uint32_t n_limbs, size_t M, s
         case ICM_FORM_F16_CRT: {
             // sized for the worst case of primes just below 2^60
             const int pf = form == ICM_FORM_F16_CRT ? (int)ICM_FORM_I8_CRT : (int)form;
-            const uint32_t P = i8_planes(pf, std::vector<uint64_t>{(1ull << 60) - 1}, K);
+            const uint64_t qworst = (1ull << 60) - 1;
+            const uint32_t P = i8_planes(pf, &qworst, 1, K);
             if (!P) return fail(ICM_EBOUND, "CRT form unavailable for this K");
             *bytes = (size_t)n_limbs * P * N * i8_kpad(K) * (form == ICM_FORM_F16_CRT ? 2 : 1);
             if (form != ICM_FORM_I8_DIGITS) *bytes += 256 + crt_scratch_bytes(n_limbs, P, N, M);
@@ -554,31 +555,32 @@ icm_status icm_ppmm(icm_form form, const uint64_t *q, uint32_t n_limbs, const ui
     if (crt_set_attributes() != cudaSuccess) return fail(ICM_ECUDA, "kernel attributes");
     cudaError_t e;
     switch (form) {
-        case ICM_FORM_U64: e = launch_ppmm_u64(lt, dev_A, dev_B, dev_C, M, N, K, (cudaStream_t)stream); break;
+        case ICM_FORM_U64: e = launch_ppmm_u64(lt, dev_A, dev_B, dev_C, M, N, K, false, (cudaStream_t)stream); break;
         case ICM_FORM_I8_DIGITS: {
             I8Consts k;
             const char *why = "";
-            if (!make_i8_consts(form, qv, K, k, &why)) return fail(ICM_EBOUND, why);
+            if (!make_i8_consts(form, qv.data(), qv.size(), K, k, &why)) return fail(ICM_EBOUND, why);
             const size_t pl = (size_t)n_limbs * 8 * N * i8_kpad(K);
             if (pl && (!dev_ws || ws_bytes < pl)) return fail(ICM_ENOMEM, "workspace too small");
             e = launch_planes(form, k, dev_B, (int8_t *)dev_ws, N, K, i8_kpad(K), (cudaStream_t)stream);
             if (e == cudaSuccess)
-                e = launch_ppmm_i8(form, k, dev_A, (const int8_t *)dev_ws, dev_C, M, N, K, i8_kpad(K), (cudaStream_t)stream);
+                e = launch_ppmm_i8(form, k, dev_A, false, (const int8_t *)dev_ws, dev_C, M, N, K, i8_kpad(K),
+                                   (cudaStream_t)stream);
             break;
         }
         case ICM_FORM_I8_CRT:
         case ICM_FORM_F16_CRT: {
             I8Consts k;
             const char *why = "";
-            if (!make_i8_consts(ICM_FORM_I8_CRT, qv, K, k, &why)) return fail(ICM_EBOUND, why);
+            if (!make_i8_consts(ICM_FORM_I8_CRT, qv.data(), qv.size(), K, k, &why)) return fail(ICM_EBOUND, why);
             const bool f16 = form == ICM_FORM_F16_CRT;
             const size_t pl = (size_t)n_limbs * k.n_mod * N * i8_kpad(K) * (f16 ? 2 : 1);
             const size_t sc = crt_scratch_bytes(n_limbs, k.n_mod, N, M);
             if ((pl || sc) && (!dev_ws || ws_bytes < align256(pl) + sc)) return fail(ICM_ENOMEM, "workspace too small");
             e = launch_crt_planes(f16, k, dev_B, dev_ws, N, K, i8_kpad(K), (cudaStream_t)stream);
             if (e == cudaSuccess)
-                e = launch_ppmm_crt(f16, 256, k, dev_A, dev_ws, dev_C, M, N, K, i8_kpad(K), (char *)dev_ws + align256(pl),
-                                    (cudaStream_t)stream);
+                e = launch_ppmm_crt(f16, 256, k, dev_A, false, dev_ws, dev_C, M, N, K, i8_kpad(K),
+                                    (char *)dev_ws + align256(pl), (cudaStream_t)stream);
             break;
         }
         default: return fail(ICM_EUNSUPPORTED, "form not built");

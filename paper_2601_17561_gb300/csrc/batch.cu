@@ -48,6 +48,7 @@ icm_status enqueue_batch(icm_ctx *c, const icm_db *const *dbs, size_t n, const i
         for (size_t i = 0; i < n; ++i) { A[i] = dbs[i]->dev; C[i] = (uint64_t *)dev_outs[i]; M[i] = dbs[i]->lay.M; }
         ChunkTab tab;
         if (!make_chunk_tab(A.data(), C.data(), M.data(), (uint32_t)n, tab)) return api_fail(ICM_EINVAL, "1..16 chunks");
+        tab.a_digits = 1;
         const void *planes = (const char *)q->dev + (size_t)c->p.n_limbs * q->n_cols * c->K * 8;
         e = launch_ppmm_crt_grouped(q->form == ICM_FORM_F16_CRT, bn, c->i8_crt, tab, planes, q->n_cols, c->K,
                                     i8_kpad(c->K), dev_ws, st);
@@ -55,9 +56,9 @@ icm_status enqueue_batch(icm_ctx *c, const icm_db *const *dbs, size_t n, const i
         for (size_t i = 0; i < n && e == cudaSuccess; ++i) {
             if (q->form == ICM_FORM_U64)
                 e = launch_ppmm_u64(c->lt, dbs[i]->dev, (const uint64_t *)q->dev, (uint64_t *)dev_outs[i], dbs[i]->lay.M,
-                                    q->n_cols, c->K, st);
+                                    q->n_cols, c->K, true, st);
             else
-                e = launch_ppmm_i8(ICM_FORM_I8_DIGITS, c->i8_digits, dbs[i]->dev,
+                e = launch_ppmm_i8(ICM_FORM_I8_DIGITS, c->i8_digits, dbs[i]->dev, true,
                                    (const int8_t *)q->dev + (size_t)c->p.n_limbs * q->n_cols * c->K * 8,
                                    (uint64_t *)dev_outs[i], dbs[i]->lay.M, q->n_cols, c->K, i8_kpad(c->K), st);
         }
@@ -152,7 +153,8 @@ icm_status icm_autotune(icm_ctx *c, const icm_db *const *dbs, size_t n_dbs, cons
                         float *ms_per_choice, size_t n_choices) {
     if (!c || !q || !best_tile_n) return api_fail(ICM_EINVAL, "bad arguments");
     if (!crt_form(q->form)) { *best_tile_n = 0; return ICM_OK; }      // single kernel variant
-    const int choices[2] = {128, 256};
+    const int choices[3] = {128, 256, ICM_CRT_TCGEN05};
+    const int n_var = q->form == ICM_FORM_F16_CRT && crt_tc_supported(c->K) ? 3 : 2;
     float best_ms = 1e30f;
     int best = c->crt_bn;
     cudaStream_t st = (cudaStream_t)stream;
@@ -160,7 +162,7 @@ icm_status icm_autotune(icm_ctx *c, const icm_db *const *dbs, size_t n_dbs, cons
     cudaEventCreate(&a);
     cudaEventCreate(&b);
     icm_status s = ICM_OK;
-    for (int i = 0; i < 2 && s == ICM_OK; ++i) {
+    for (int i = 0; i < n_var && s == ICM_OK; ++i) {
         c->crt_bn = choices[i];
         std::vector<icm_scores *> outs(n_dbs, nullptr);
         cudaEventRecord(a, st);
@@ -179,7 +181,21 @@ icm_status icm_autotune(icm_ctx *c, const icm_db *const *dbs, size_t n_dbs, cons
     cudaEventDestroy(b);
     c->crt_bn = best;
     *best_tile_n = best;
+    if (s == ICM_OK && device_status(true) != 0) return api_fail(ICM_ETIMEOUT, "a kernel gave up a bounded wait");
     return s;
+}
+
+icm_status icm_ctx_set_variant(icm_ctx *c, int variant) {
+    if (!c || (variant != 0 && variant != ICM_CRT_TCGEN05 && variant != 128 && variant != 256))
+        return api_fail(ICM_EINVAL, "variant must be 0, 1 or 128");
+    c->crt_bn = variant == 0 ? 256 : variant;
+    return ICM_OK;
+}
+
+icm_status icm_device_status(int clear) {
+    const uint32_t v = device_status(clear != 0);
+    if (v == 0xFFFFFFFFu) return api_fail(ICM_ECUDA, "status word unreadable");
+    return v ? api_fail(ICM_ETIMEOUT, "a kernel gave up a bounded wait") : ICM_OK;
 }
 
 }  // extern "C"

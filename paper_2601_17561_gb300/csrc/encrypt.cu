@@ -8,6 +8,7 @@
 //   W[r][d2 + j] = (M_db S_q)[r][j] for j < N_q (S_q: vertical stack of the negacyclic matrices
 //   of the query secrets).  The gadget factor Q' makes Q' * Q = 0 modulo Q_db, which removes
 //   the query's wrap-around multiple of Q from the decrypted product.
+// Stored rows are written in the balanced-digit form of icm_device.cuh (to_digit_form).
 // Query eyes, MSRLWE form modulo Q (Section 2.3):
 //   b_{t,j} = -(s_{q,t} * a_j) + Delta * c'_j[t N_q .. (t+1) N_q) + e_{t,j},  a_j uniform mod Q,
 //   where column j = eye * rho + r holds rotation r of the eye (Section 2.1.2).
@@ -122,7 +123,7 @@ __global__ void __launch_bounds__(1024) k_db_apart_b(DbEncArgs a) {
     for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) {
         const uint64_t v = uniform_mod(sm64(ka, (uint64_t)i * a.K + k), q);
         acol[i] = v;
-        dbl[(size_t)i * a.K + k] = v;
+        dbl[(size_t)i * a.K + k] = to_digit_form(v, q);
     }
     for (uint32_t x = threadIdx.x; x < a.n_blocks * a.h; x += blockDim.x) { spos[x] = a.sdb_pos[x]; ssgn[x] = a.sdb_sgn[x]; }
     __syncthreads();
@@ -145,7 +146,7 @@ __global__ void __launch_bounds__(1024) k_db_apart_b(DbEncArgs a) {
         const int e = cbd_sample(sm64(ke, r * a.K + k), a.eta);
         uint64_t v = sub_mod(*dst, sa, q);
         v = e >= 0 ? add_mod(v, (uint64_t)e, q) : sub_mod(v, (uint64_t)(-e), q);
-        *dst = v;
+        *dst = to_digit_form(v, q);
     }
 }
 

@@ -66,6 +66,22 @@ __device__ __forceinline__ uint64_t reduce_s64(int64_t x, uint64_t q, uint64_t r
     return m ? q - m : 0;
 }
 
+// ---------------------------------------------------------------- balanced-digit storage form
+
+// The database stores each residue x in [0, q) as the word z whose bytes are the signed balanced
+// base-256 digits d_t in [-128, 127] of its centred lift c (c = x or x - q, |c| < q/2 < 2^59):
+// c = sum_t d_t 256^t, and the bytes of c + 0x80..80 are d_t + 128, so z = (c + B) ^ B with
+// B = 0x8080808080808080.  Tensor-core forms read the digits directly; the u64 form maps back.
+#define ICM_DIGIT_BIAS 0x8080808080808080ull
+__host__ __device__ __forceinline__ uint64_t to_digit_form(uint64_t x, uint64_t q) {
+    const uint64_t c = (x > (q >> 1)) ? x - q : x;            // two's complement centred lift
+    return (c + ICM_DIGIT_BIAS) ^ ICM_DIGIT_BIAS;
+}
+__host__ __device__ __forceinline__ uint64_t from_digit_form(uint64_t z, uint64_t q) {
+    const uint64_t c = (z ^ ICM_DIGIT_BIAS) - ICM_DIGIT_BIAS;
+    return ((int64_t)c < 0) ? c + q : c;
+}
+
 // ---------------------------------------------------------------- bounded device waits
 
 // Device status word values written by kernels that give up a bounded wait or find bad input.

@@ -109,7 +109,7 @@ cudaError_t launch_query_encrypt(const icm_ctx *c, const uint8_t *d_codes, const
 cudaError_t launch_query_extend(const icm_ctx *c, const uint64_t *d_ct, uint32_t n_cols, uint64_t *d_op,
                                 cudaStream_t st);
 cudaError_t launch_ppmm_u64(const LimbTable &lt, const uint64_t *A, const uint64_t *B, uint64_t *C,
-                            uint64_t M, uint64_t N, uint64_t K, cudaStream_t st);
+                            uint64_t M, uint64_t N, uint64_t K, bool a_digits, cudaStream_t st);
 cudaError_t launch_fold(const icm_ctx *c, const LayoutDev &lay, const uint64_t *d_in, uint32_t n_eyes,
                         uint64_t *d_out, cudaStream_t st);
 cudaError_t launch_decrypt(const icm_ctx *c, const LayoutDev &lay, const uint64_t *d_scores, uint32_t n_cols,

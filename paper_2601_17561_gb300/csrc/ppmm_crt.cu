@@ -75,14 +75,16 @@ __device__ __forceinline__ void mma(int (&c)[4], const uint32_t (&a)[4], const u
                  : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-// Centred residue (|r| <= m/2 + 1) of the centred lift of x modulo m: the bytes of
-// lift(x) + 0x80..80 are the balanced digits d_t + 128, and lift(x) = sum_t d_t 256^t, so two dp4a
-// against the centred constants w_t = 256^t mod m give a representative of |s| <= 2^17.
-__device__ __forceinline__ int crt_residue(uint64_t x, uint64_t q, int m, int wlo, int whi, float inv_m) {
-    const uint64_t y = ((x > (q >> 1)) ? x - q : x) + 0x8080808080808080ull;
-    int s = __dp4a((int)((uint32_t)y ^ 0x80808080u), wlo, 0);
-    s = __dp4a((int)((uint32_t)(y >> 32) ^ 0x80808080u), whi, s);
+// Centred residue (|r| <= m/2) modulo m of a residue given by its balanced digits z (the storage
+// form of the database): lift(x) = sum_t d_t 256^t, so two dp4a against the centred constants
+// w_t = 256^t mod m give a representative s with |s| <= 2^17, then one rounding step.
+__device__ __forceinline__ int crt_residue_z(uint64_t z, int m, int wlo, int whi, float inv_m) {
+    int s = __dp4a((int)(uint32_t)z, wlo, 0);
+    s = __dp4a((int)(uint32_t)(z >> 32), whi, s);
     return s - m * __float2int_rn((float)s * inv_m);
+}
+__device__ __forceinline__ int crt_residue(uint64_t x, uint64_t q, int m, int wlo, int whi, float inv_m) {
+    return crt_residue_z(to_digit_form(x, q), m, wlo, whi, inv_m);
 }
 
 // 4 residues -> packed operand bits (int8: one word, fp16: two words)
@@ -162,7 +164,8 @@ __global__ void __launch_bounds__(NT, 1) k_crt_p1(P1Args p) {
             const int idx = tid + e * NT, row = idx >> 3, g = idx & 7;
             int v[4];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) v[j] = crt_residue(ra[e][j], q, m, wlo, whi, inv_m);
+            for (int j = 0; j < 4; ++j)
+                v[j] = p.tab.a_digits ? crt_residue_z(ra[e][j], m, wlo, whi, inv_m) : crt_residue(ra[e][j], q, m, wlo, whi, inv_m);
             uint32_t w[2];
             pack4<F16>(v, w);
             unsigned char *dst = sA + (size_t)st * BM * LDB + row * LDB + g * 4 * ESZ;
@@ -332,7 +335,8 @@ cudaError_t run_p1(const P1Args &a, cudaStream_t st) {
 namespace icm {
 
 cudaError_t crt_set_attributes() {
-    cudaError_t e = set_p1_attr<true, 128>();
+    cudaError_t e = crt_tc_set_attributes();
+    if (e == cudaSuccess) e = set_p1_attr<true, 128>();
     if (e == cudaSuccess) e = set_p1_attr<true, 256>();
     if (e == cudaSuccess) e = set_p1_attr<false, 128>();
     if (e == cudaSuccess) e = set_p1_attr<false, 256>();
@@ -347,6 +351,7 @@ bool make_chunk_tab(const uint64_t *const *A, uint64_t *const *C, const uint64_t
     if (n == 0 || n > ICM_MAX_CHUNKS) return false;
     t = ChunkTab{};
     t.n = n;
+    t.a_digits = 1;
     t.row0[0] = 0;
     t.mt0[0] = 0;
     for (uint32_t c = 0; c < n; ++c) {
@@ -373,6 +378,9 @@ cudaError_t launch_ppmm_crt_grouped(bool f16, int bn, const I8Consts &k, const C
                                     uint64_t K, uint64_t Kp, void *scratch, cudaStream_t st) {
     const uint64_t Mall = tab.row0[tab.n];
     if (Mall == 0 || N == 0) return cudaSuccess;
+    if (f16 && bn == ICM_CRT_TCGEN05 && tab.a_digits && crt_tc_supported(K))
+        return launch_ppmm_crt_tc(k, tab, Bp, N, K, Kp, scratch, st);
+    if (bn != 128) bn = 256;
     for (uint64_t n0 = 0; n0 < N; n0 += NCHUNK) {
         const uint64_t nch = std::min<uint64_t>(NCHUNK, N - n0);
         P1Args a{};
@@ -385,18 +393,25 @@ cudaError_t launch_ppmm_crt_grouped(bool f16, int bn, const I8Consts &k, const C
         if (f16) e = bn == 128 ? run_p1<true, 128>(a, st) : run_p1<true, 256>(a, st);
         else e = bn == 128 ? run_p1<false, 128>(a, st) : run_p1<false, 256>(a, st);
         if (e != cudaSuccess) return e;
-        P2Args b{tab, reinterpret_cast<const uint8_t *>(scratch), N, n0, nch, k};
-        k_crt_combine<<<dim3((unsigned)((nch * Mall + 255) / 256), k.n_limbs), 256, 0, st>>>(b);
-        e = cudaGetLastError();
+        e = launch_crt_combine(k, tab, scratch, N, n0, nch, st);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
 
-cudaError_t launch_ppmm_crt(bool f16, int bn, const I8Consts &k, const uint64_t *A, const void *Bp, uint64_t *C,
-                            uint64_t M, uint64_t N, uint64_t K, uint64_t Kp, void *scratch, cudaStream_t st) {
+cudaError_t launch_crt_combine(const I8Consts &k, const ChunkTab &tab, const void *scratch, uint64_t N, uint64_t n0,
+                               uint64_t nch, cudaStream_t st) {
+    const uint64_t Mall = tab.row0[tab.n];
+    P2Args b{tab, reinterpret_cast<const uint8_t *>(scratch), N, n0, nch, k};
+    k_crt_combine<<<dim3((unsigned)((nch * Mall + 255) / 256), k.n_limbs), 256, 0, st>>>(b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ppmm_crt(bool f16, int bn, const I8Consts &k, const uint64_t *A, bool a_digits, const void *Bp,
+                            uint64_t *C, uint64_t M, uint64_t N, uint64_t K, uint64_t Kp, void *scratch, cudaStream_t st) {
     ChunkTab tab;
     make_chunk_tab(&A, &C, &M, 1, tab);
+    tab.a_digits = a_digits ? 1 : 0;
     return launch_ppmm_crt_grouped(f16, bn, k, tab, Bp, N, K, Kp, scratch, st);
 }
 

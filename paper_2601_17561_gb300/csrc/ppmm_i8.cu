@@ -34,11 +34,12 @@ constexpr int BM = 128, BN = 64, BK = 32, NT = 256;
 constexpr int MT = BM / 16, NTL = BN / 8;     // m16 and n8 tiles per block
 
 struct I8Args {
-    const uint64_t *A;      // [L][M][K] canonical residues
+    const uint64_t *A;      // [L][M][K] residues, canonical or balanced-digit form (a_digits)
     const int8_t *Bp;       // [L][P][N][Kp] planes
     uint64_t *C;            // [L][N][M]
     uint64_t M, N, K, Kp;
     icm::I8Consts k;
+    int a_digits;
 };
 
 __device__ __forceinline__ void mma_s8(int (&c)[4], const uint4 &a, const uint2 &b) {
@@ -49,15 +50,13 @@ __device__ __forceinline__ void mma_s8(int (&c)[4], const uint4 &a, const uint2 
 
 // Balanced digits of the centred lift of 4 residues (same row, 4 consecutive k): out[t] packs
 // digit t of the 4 values (k ascending in bytes 0..3).
-__device__ __forceinline__ void digits4(const uint64_t (&x)[4], uint64_t q, uint32_t (&out)[8]) {
+__device__ __forceinline__ void digits4(const uint64_t (&x)[4], uint64_t q, bool in_digits, uint32_t (&out)[8]) {
     uint32_t lo[4], hi[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-        const uint64_t v = x[e];
-        const uint64_t c = (v > (q >> 1)) ? v - q : v;            // centred lift, two's complement
-        const uint64_t y = c + 0x8080808080808080ull;               // bytes = d_t + 128
-        lo[e] = (uint32_t)y ^ 0x80808080u;
-        hi[e] = (uint32_t)(y >> 32) ^ 0x80808080u;
+        const uint64_t z = in_digits ? x[e] : to_digit_form(x[e], q);   // bytes = signed digits d_t
+        lo[e] = (uint32_t)z;
+        hi[e] = (uint32_t)(z >> 32);
     }
     // gather byte t of the four words
     const uint32_t a01 = __byte_perm(lo[0], lo[1], 0x5140), a23 = __byte_perm(lo[2], lo[3], 0x5140);
@@ -137,7 +136,7 @@ __global__ void __launch_bounds__(NT, 1) k_ppmm_i8(I8Args p) {
                     const int reg = (rr >> 3) + ((g >> 2) << 1), ln = ((rr & 7) << 2) + (g & 3);
                     if (FORM == 0) {
                         uint32_t d[8];
-                        digits4(x, q, d);
+                        digits4(x, q, p.a_digits != 0, d);
                         for (int t = t_lo; t <= t_hi; ++t) sA[t][mt][ln][reg] = d[t];
                     } else {
                         const int m = p.k.mod[pass];
@@ -266,10 +265,10 @@ cudaError_t launch_planes(int form, const I8Consts &k, const uint64_t *op, int8_
     return cudaGetLastError();
 }
 
-cudaError_t launch_ppmm_i8(int form, const I8Consts &k, const uint64_t *A, const int8_t *Bp, uint64_t *C, uint64_t M,
-                           uint64_t N, uint64_t K, uint64_t Kp, cudaStream_t st) {
+cudaError_t launch_ppmm_i8(int form, const I8Consts &k, const uint64_t *A, bool a_digits, const int8_t *Bp, uint64_t *C,
+                           uint64_t M, uint64_t N, uint64_t K, uint64_t Kp, cudaStream_t st) {
     if (M == 0 || N == 0) return cudaSuccess;
-    I8Args a{A, Bp, C, M, N, K, Kp, k};
+    I8Args a{A, Bp, C, M, N, K, Kp, k, a_digits ? 1 : 0};
     dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((N + BN - 1) / BN), k.n_limbs);
     k_ppmm_i8<0><<<grid, NT, 0, st>>>(a);
     return cudaGetLastError();
@@ -297,32 +296,33 @@ int64_t inv_h(int64_t a, int64_t m) {
 }
 uint64_t shoup_h(uint64_t w, uint64_t q) { return (uint64_t)(((u128)w << 64) / q); }
 
-// Greedy: the largest pairwise-coprime integers <= 256, as many as the range needs.
-std::vector<int> crt_moduli(const std::vector<uint64_t> &q, uint64_t K) {
+// Greedy: the largest pairwise-coprime integers <= 256, as many as the range needs.  Fills mods
+// and returns their count (0 if no set within ICM_MAX_MODULI covers the range); no allocation.
+uint32_t crt_moduli(const uint64_t *q, size_t nq, uint64_t K, int (&mods)[ICM_MAX_MODULI]) {
     uint64_t qmax = 0;
-    for (uint64_t v : q) qmax = v > qmax ? v : qmax;
+    for (size_t i = 0; i < nq; ++i) qmax = q[i] > qmax ? q[i] : qmax;
     // |C| <= K ((qmax-1)/2)^2; need log2 M >= 1 + log2|C| + 8 (kappa margin)
     const double need = 1.0 + std::log2((double)(K ? K : 1)) + 2.0 * std::log2((double)((qmax - 1) / 2 + 1)) + 8.0;
-    std::vector<int> mods;
+    uint32_t n = 0;
     double have = 0;
-    for (int n = 256; n >= 3 && have < need && mods.size() < ICM_MAX_MODULI; --n) {
+    for (int v = 256; v >= 3 && have < need && n < ICM_MAX_MODULI; --v) {
         bool ok = true;
-        for (int m : mods) if (gcd_h((uint64_t)n, (uint64_t)m) != 1) { ok = false; break; }
-        if (ok) { mods.push_back(n); have += std::log2((double)n); }
+        for (uint32_t i = 0; i < n; ++i) if (gcd_h((uint64_t)v, (uint64_t)mods[i]) != 1) { ok = false; break; }
+        if (ok) { mods[n++] = v; have += std::log2((double)v); }
     }
-    if (have < need) mods.clear();
-    return mods;
+    return have < need ? 0 : n;
 }
 }  // namespace
 
-uint32_t i8_planes(int form, const std::vector<uint64_t> &q, uint64_t K) {
-    return form == ICM_FORM_I8_DIGITS ? 8u : (uint32_t)crt_moduli(q, K).size();
+uint32_t i8_planes(int form, const uint64_t *q, size_t nq, uint64_t K) {
+    int mods[ICM_MAX_MODULI];
+    return form == ICM_FORM_I8_DIGITS ? 8u : crt_moduli(q, nq, K, mods);
 }
 
-bool make_i8_consts(int form, const std::vector<uint64_t> &q, uint64_t K, I8Consts &k, const char **why) {
+bool make_i8_consts(int form, const uint64_t *q, size_t nq, uint64_t K, I8Consts &k, const char **why) {
     k = I8Consts{};
-    k.n_limbs = (uint32_t)q.size();
-    for (size_t l = 0; l < q.size(); ++l) {
+    k.n_limbs = (uint32_t)nq;
+    for (size_t l = 0; l < nq; ++l) {
         if (q[l] >= (1ull << 60)) { *why = "int8 forms need primes below 2^60 (8 balanced digits)"; return false; }
         k.q[l] = q[l];
         k.r64[l] = (uint64_t)(((u128)1 << 64) / q[l]);
@@ -335,10 +335,11 @@ bool make_i8_consts(int form, const std::vector<uint64_t> &q, uint64_t K, I8Cons
     }
     // CRT form: every int32 accumulator sums K products of magnitude <= 2^14
     if (K * 16384ull > 2147483647ull) { *why = "K too deep for int32 accumulation of the CRT form (K <= 131071)"; return false; }
-    std::vector<int> mods = crt_moduli(q, K);
-    if (mods.empty()) { *why = "no set of small moduli covers the product range"; return false; }
-    k.n_mod = (uint32_t)mods.size();
-    for (size_t i = 0; i < mods.size(); ++i) {
+    int mods[ICM_MAX_MODULI];
+    const uint32_t nm = crt_moduli(q, nq, K, mods);
+    if (nm == 0) { *why = "no set of small moduli covers the product range"; return false; }
+    k.n_mod = nm;
+    for (uint32_t i = 0; i < nm; ++i) {
         const int m = mods[i];
         int w[8];
         for (int t = 0; t < 8; ++t) {
@@ -353,18 +354,18 @@ bool make_i8_consts(int form, const std::vector<uint64_t> &q, uint64_t K, I8Cons
         k.inv_m[i] = 1.0f / (float)m;
         // (M / m_i) mod m_i and its inverse
         uint64_t hat = 1;
-        for (size_t j = 0; j < mods.size(); ++j) if (j != i) hat = hat * (uint64_t)mods[j] % (uint64_t)m;
+        for (uint32_t j = 0; j < nm; ++j) if (j != i) hat = hat * (uint64_t)mods[j] % (uint64_t)m;
         k.yinv[i] = (int32_t)inv_h((int64_t)hat, m);
-        for (size_t l = 0; l < q.size(); ++l) {
+        for (size_t l = 0; l < nq; ++l) {
             uint64_t W = 1 % q[l];
-            for (size_t j = 0; j < mods.size(); ++j) if (j != i) W = mulmod_h(W, (uint64_t)mods[j], q[l]);
+            for (uint32_t j = 0; j < nm; ++j) if (j != i) W = mulmod_h(W, (uint64_t)mods[j], q[l]);
             k.W[l][i] = W;
             k.Ws[l][i] = shoup_h(W, q[l]);
         }
     }
-    for (size_t l = 0; l < q.size(); ++l) {
+    for (size_t l = 0; l < nq; ++l) {
         uint64_t Mq = 1 % q[l];
-        for (int m : mods) Mq = mulmod_h(Mq, (uint64_t)m, q[l]);
+        for (uint32_t j = 0; j < nm; ++j) Mq = mulmod_h(Mq, (uint64_t)mods[j], q[l]);
         k.Mq[l] = Mq;
         k.Mqs[l] = shoup_h(Mq, q[l]);
     }

@@ -25,9 +25,9 @@ struct I8Consts {
 
 // Builds the constants for primes q and contraction depth K; returns false (with a reason in
 // `why`) if the int32 overflow invariant or the CRT range cannot be met.
-bool make_i8_consts(int form, const std::vector<uint64_t> &q, uint64_t K, I8Consts &out, const char **why);
+bool make_i8_consts(int form, const uint64_t *q, size_t nq, uint64_t K, I8Consts &out, const char **why);
 // Planes per residue: 8 digit planes or n_mod residue planes.
-uint32_t i8_planes(int form, const std::vector<uint64_t> &q, uint64_t K);
+uint32_t i8_planes(int form, const uint64_t *q, size_t nq, uint64_t K);
 inline uint64_t i8_kpad(uint64_t K) { return (K + 31) / 32 * 32; }
 
 cudaError_t launch_planes(int form, const I8Consts &k, const uint64_t *op, int8_t *planes, uint64_t N, uint64_t K,
@@ -41,18 +41,29 @@ struct ChunkTab {
     uint64_t M[ICM_MAX_CHUNKS];
     uint64_t row0[ICM_MAX_CHUNKS + 1];     // prefix sums of M_c
     uint32_t mt0[ICM_MAX_CHUNKS + 1];      // prefix sums of 128-row tiles
+    int a_digits;                          // A in the balanced-digit storage form (else canonical)
 };
 bool make_chunk_tab(const uint64_t *const *A, uint64_t *const *C, const uint64_t *M, uint32_t n, ChunkTab &t);
 cudaError_t launch_ppmm_crt_grouped(bool f16, int bn, const I8Consts &k, const ChunkTab &tab, const void *Bp, uint64_t N,
                                     uint64_t K, uint64_t Kp, void *scratch, cudaStream_t st);
 cudaError_t crt_set_attributes();
+// Kernel variants of the CRT product (the column tile of the mma.sync kernel, or the tcgen05
+// kernel for the fp16 form on the balanced-digit database).
+#define ICM_CRT_TCGEN05 1
+cudaError_t launch_crt_combine(const I8Consts &k, const ChunkTab &tab, const void *scratch, uint64_t N, uint64_t n0,
+                               uint64_t nch, cudaStream_t st);
+cudaError_t crt_tc_set_attributes();
+bool crt_tc_supported(uint64_t K);
+cudaError_t launch_ppmm_crt_tc(const I8Consts &k, const ChunkTab &tab, const void *Bp, uint64_t N, uint64_t K, uint64_t Kp,
+                               void *scratch, cudaStream_t st);
+uint32_t device_status(bool clear);
 // small-modulus CRT forms (int8 or fp16 operands): query residue planes, two-phase product
 uint64_t crt_scratch_bytes(uint32_t n_limbs, uint32_t n_mod, uint64_t N, uint64_t M);
 cudaError_t launch_crt_planes(bool f16, const I8Consts &k, const uint64_t *op, void *planes, uint64_t N, uint64_t K,
                               uint64_t Kp, cudaStream_t st);
-cudaError_t launch_ppmm_crt(bool f16, int bn, const I8Consts &k, const uint64_t *A, const void *Bp, uint64_t *C,
-                            uint64_t M, uint64_t N, uint64_t K, uint64_t Kp, void *scratch, cudaStream_t st);
-cudaError_t launch_ppmm_i8(int form, const I8Consts &k, const uint64_t *A, const int8_t *Bp, uint64_t *C, uint64_t M,
-                           uint64_t N, uint64_t K, uint64_t Kp, cudaStream_t st);
+cudaError_t launch_ppmm_crt(bool f16, int bn, const I8Consts &k, const uint64_t *A, bool a_digits, const void *Bp,
+                            uint64_t *C, uint64_t M, uint64_t N, uint64_t K, uint64_t Kp, void *scratch, cudaStream_t st);
+cudaError_t launch_ppmm_i8(int form, const I8Consts &k, const uint64_t *A, bool a_digits, const int8_t *Bp, uint64_t *C,
+                           uint64_t M, uint64_t N, uint64_t K, uint64_t Kp, cudaStream_t st);
 
 }  // namespace icm

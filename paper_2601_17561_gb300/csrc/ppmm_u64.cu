@@ -8,6 +8,9 @@
 // K loop: U_2 gains three products per k, 3 K 2^40 < 2^64 for K < 2^22.  The epilogue reduces
 // sum_s U_s 2^(20 s) modulo q_l with Shoup multiplications by the constants 2^(20 s) mod q_l.
 //
+// A arrives either canonical or in the balanced-digit storage form of the database (mapped back to
+// canonical on load).
+//
 // Tiling: a 64 x 64 output tile per 256-thread block, 4 x 4 outputs per thread, K in steps of
 // 16.  Global loads are coalesced along K (both operands are K-contiguous); the tile is split
 // into limbs once on its way into shared memory (stored k-major so that a thread reads its four
@@ -24,6 +27,7 @@ struct PpmmArgs {
     uint64_t *C;
     uint64_t M, N, K;
     LimbTable lt;
+    int a_digits;            // A stored in the balanced-digit form
 };
 
 __global__ void __launch_bounds__(NT, 1) k_ppmm_u64(PpmmArgs p) {
@@ -35,6 +39,7 @@ __global__ void __launch_bounds__(NT, 1) k_ppmm_u64(PpmmArgs p) {
     const uint64_t *Al = p.A + (size_t)l * M * K;
     const uint64_t *Bl = p.B + (size_t)l * N * K;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const uint64_t q = p.lt.q[l], r64 = p.lt.r64[l];
 
     uint64_t acc[4][4][5];
 #pragma unroll
@@ -50,7 +55,8 @@ __global__ void __launch_bounds__(NT, 1) k_ppmm_u64(PpmmArgs p) {
         for (int e = 0; e < 4; ++e) {
             const int idx = tid + e * NT, r = idx >> 4, kk = idx & 15;
             const uint64_t k = k0 + kk;
-            ra[e] = (m0 + r < M && k < K) ? __ldg(Al + (m0 + r) * K + k) : 0ull;
+            ra[e] = (m0 + r < M && k < K) ? (p.a_digits ? from_digit_form(__ldg(Al + (m0 + r) * K + k), q)
+                                                        : __ldg(Al + (m0 + r) * K + k)) : 0ull;
             rb[e] = (n0 + r < N && k < K) ? __ldg(Bl + (n0 + r) * K + k) : 0ull;
         }
     };
@@ -107,7 +113,6 @@ __global__ void __launch_bounds__(NT, 1) k_ppmm_u64(PpmmArgs p) {
     }
 
     // epilogue: sum_s U_s 2^(20 s) mod q
-    const uint64_t q = p.lt.q[l], r64 = p.lt.r64[l];
     uint64_t *Cl = p.C + (size_t)l * N * M;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -133,9 +138,9 @@ __global__ void __launch_bounds__(NT, 1) k_ppmm_u64(PpmmArgs p) {
 namespace icm {
 
 cudaError_t launch_ppmm_u64(const LimbTable &lt, const uint64_t *A, const uint64_t *B, uint64_t *C,
-                            uint64_t M, uint64_t N, uint64_t K, cudaStream_t st) {
+                            uint64_t M, uint64_t N, uint64_t K, bool a_digits, cudaStream_t st) {
     if (M == 0 || N == 0) return cudaSuccess;
-    PpmmArgs p{A, B, C, M, N, K, lt};
+    PpmmArgs p{A, B, C, M, N, K, lt, a_digits ? 1 : 0};
     dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((N + BN - 1) / BN), lt.n);
     k_ppmm_u64<<<grid, NT, 0, st>>>(p);
     return cudaGetLastError();

@@ -68,10 +68,22 @@ def test_query_operand_bit_exact(tiny, gpu_run):
     assert np.array_equal(got, tiny["Bq"])
 
 
+def _from_digit_form(z: np.ndarray, q) -> np.ndarray:
+    """The database's storage word holds the signed balanced base-256 digits of the centred lift
+    (bytes in two's complement): lift = (z xor 0x80..80) - 0x80..80 (mod 2^64)."""
+    B = np.uint64(0x8080808080808080)
+    c = (z ^ B) - B                                      # wraps modulo 2^64
+    out = np.empty_like(z)
+    for l, ql in enumerate(q):
+        cl = c[l].view(np.int64)
+        out[l] = np.where(cl < 0, (cl + np.int64(ql)).view(np.uint64), c[l])
+    return out
+
+
 def test_database_bit_exact(tiny, gpu_run):
     A = tiny["A"]
     assert gpu_run["db"].m_rows == A.shape[1]
-    got = _u64(gpu_run["db"].buf, A.shape)
+    got = _from_digit_form(_u64(gpu_run["db"].buf, A.shape), tiny["P"].q)
     assert np.array_equal(got, A)
 
 
@@ -179,3 +191,19 @@ def test_ppmm_extremes(form, kind):
                  torch.from_numpy(Bm.view(np.int64)).cuda()).cpu().numpy().view(np.uint64)
     for l, q_l in enumerate(q):
         assert np.all(got[l] == (xc[l] * xc[l] * K) % q_l)
+
+
+def test_ccmm_tcgen05_variant_bit_exact(tiny, gpu_run):
+    """The tcgen05 kernel variant of the fp16 CRT form (tensor-memory accumulators) gives the
+    oracle's residues, and no kernel gave up a bounded wait."""
+    from paper_2601_17561_gb300 import icm as C
+    eng, W = gpu_run["eng"], tiny["W"]
+    C.icm_ctx_set_variant(eng.ctx, 1)
+    try:
+        q = eng.prepare(gpu_run["ct"], W.q_codes.shape[0], "f16_crt")
+        s = eng.match(gpu_run["db"], q)
+        torch.cuda.synchronize()
+        C.icm_device_status(True)
+        assert np.array_equal(s.residues(), tiny["C"])
+    finally:
+        C.icm_ctx_set_variant(eng.ctx, 0)
