@@ -22,9 +22,11 @@
  *    handles made from it.  Handles are immutable after creation and may be shared across
  *    streams; icm_ctx_create/icm_keygen are not thread-safe on the same context.
  *
- * Data layouts (u64 residues are canonical, in [0, q_l))
+ * Data layouts (u64 residues are canonical, in [0, q_l), unless stated otherwise)
  *  - Templates: `code_bits / 8` bytes per code and per mask, bit b at byte b/8, bit b%8.
- *  - Database chunk: [L][M][K] u64, K = d2 + N_q, M = N_db + (stored b-rows).  Row order: the
+ *  - Database chunk: [L][M][K] u64 words, K = d2 + N_q, M = N_db + (stored b-rows).  Each word holds
+ *    the residue in balanced-digit form: its bytes (two's complement) are the digits d_t in
+ *    [-128, 127] of the centred lift c = sum_t d_t 256^t (c = (word ^ 0x80..80) - 0x80..80).  Row order: the
  *    N_db a-part rows, then the b-rows of every full block, then for a partial last block its
  *    real rows followed by the wrap-around tail coefficients [max(n_t, N_db - rho + 1), N_db)
  *    (encryptions of zero that the fold's negacyclic shift reads).
@@ -206,10 +208,19 @@ icm_status icm_plan_create(icm_ctx *ctx, const icm_db *const *dbs, size_t n_dbs,
 icm_status icm_plan_launch(icm_plan *plan, void *stream);
 void icm_plan_destroy(icm_plan *plan);
 
+/* Kernel variant of the CRT forms' product: 0 = mma.sync with 256-column tiles (default),
+ * 1 = tcgen05 (fp16 form only; tensor-memory accumulators; needs an even K, else variant 0 runs),
+ * 128 = mma.sync with 128-column tiles.  Results are identical; only speed differs. */
+icm_status icm_ctx_set_variant(icm_ctx *ctx, int variant);
+/* Device status word shared by the library's kernels: ICM_OK, or ICM_ETIMEOUT once a kernel gave
+ * up one of its bounded waits (the kernel then stopped early, so its outputs are invalid).  Reads
+ * the word (synchronising the device) and clears it when clear != 0. */
+icm_status icm_device_status(int clear);
+
 /* Autotuner: times every column-tile variant of the CRT product kernel on the caller's batch
  * (one icm_match_batch per variant, CUDA events on `stream`), keeps the fastest for the context
  * and reports it (0 for forms with a single variant).  ms_per_choice (optional) receives the
- * time of each variant (128 then 256 columns). */
+ * time of each variant in the order 128-column mma.sync, 256-column mma.sync, tcgen05 (fp16). */
 icm_status icm_autotune(icm_ctx *ctx, const icm_db *const *dbs, size_t n_dbs, const icm_query *q,
                         void *const *dev_outs, const size_t *out_bytes, void *dev_ws, size_t ws_bytes, void *stream,
                         int *best_tile_n, float *ms_per_choice, size_t n_choices);

@@ -62,6 +62,8 @@ _SIGS = {
     "icm_ppmm_workspace_bytes": (_i32, [_i32, _u32, _sz, _sz, _sz, ctypes.POINTER(_sz)]),
     "icm_ppmm": (_i32, [_i32, _vp, _u32, _vp, _vp, _vp, _sz, _sz, _sz, _vp, _sz, _vp]),
     "icm_sync": (_i32, [_vp, _u32]),
+    "icm_ctx_set_variant": (_i32, [_vp, _i32]),
+    "icm_device_status": (_i32, [_i32]),
     "icm_match_host_workspace_bytes": (_i32, [_vp, _vp, _sz, _i32, ctypes.POINTER(_sz)]),
     "icm_match_host": (_i32, [_vp, _vp, _vp, _sz, _i32, _vp, _vp, _sz, _vp]),
     "icm_probe_peak": (_i32, [_i32, ctypes.POINTER(ctypes.c_double), _vp]),
@@ -308,10 +310,18 @@ def icm_plan_destroy(plan):
 
 def icm_autotune(ctx, dbs, q, dev_outs, out_bytes, dev_ws, ws_bytes, stream=None):
     best = ctypes.c_int()
-    ms = (ctypes.c_float * 2)()
+    ms = (ctypes.c_float * 3)()
     _check(lib().icm_autotune(ctx, _handle_array(dbs), len(dbs), q, _ptr_array(dev_outs), _size_array(out_bytes),
-                              _ptr(dev_ws), ws_bytes, _stream(stream), ctypes.byref(best), ms, 2), "icm_autotune")
+                              _ptr(dev_ws), ws_bytes, _stream(stream), ctypes.byref(best), ms, 3), "icm_autotune")
     return best.value, list(ms)
+
+
+def icm_ctx_set_variant(ctx, variant: int):
+    _check(lib().icm_ctx_set_variant(ctx, variant), "icm_ctx_set_variant")
+
+
+def icm_device_status(clear: bool = True):
+    _check(lib().icm_device_status(1 if clear else 0), "icm_device_status")
 
 
 def icm_server_device_bytes(ctx, dbs, cfg):
