@@ -290,6 +290,19 @@ icm_status icm_ppmm(icm_form form, const uint64_t *q, uint32_t n_limbs, const ui
                     const uint64_t *dev_B, uint64_t *dev_C, size_t M, size_t N, size_t K,
                     void *dev_ws, size_t ws_bytes, void *stream);
 
+/* Same product as icm_ppmm for the CRT forms (ICM_FORM_I8_CRT, ICM_FORM_F16_CRT), for callers
+ * that cannot allocate device memory: it allocates nothing and takes no workspace.  The paper has
+ * no counterpart; this serves hosts whose framework owns every device allocation, code running
+ * under a fixed device-memory budget, or code enqueued while allocations are not allowed.  The
+ * workspace (query residue planes and per-modulus residue scratch) lives in one static device
+ * array of 64 MiB that every GPU loading this library holds until the process exits; problems
+ * whose workspace exceeds it are rejected with ICM_ENOMEM before any work.  The first call on a
+ * device looks up that device's address of the array (make it before any stream capture); later
+ * calls reuse it.  All calls share the array: calls that overlap on the GPU race with each other
+ * (serialise them, for instance on one stream).  Arguments as icm_ppmm minus the workspace. */
+icm_status icm_ppmm_noalloc(icm_form form, const uint64_t *q, uint32_t n_limbs, const uint64_t *dev_A,
+                            const uint64_t *dev_B, uint64_t *dev_C, size_t M, size_t N, size_t K, void *stream);
+
 /* ---------------------------------------------------------------- measurement ---- */
 
 /* Peak-rate probe used as a roofline denominator (no counterpart in the paper): runs an

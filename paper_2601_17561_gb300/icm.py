@@ -62,6 +62,7 @@ _SIGS = {
     "icm_ppmm_workspace_bytes": (_i32, [_i32, _u32, _sz, _sz, _sz, ctypes.POINTER(_sz)]),
     "icm_ppmm": (_i32, [_i32, _vp, _u32, _vp, _vp, _vp, _sz, _sz, _sz, _vp, _sz, _vp]),
     "icm_sync": (_i32, [_vp, _u32]),
+    "icm_ppmm_noalloc": (_i32, [_i32, _vp, _u32, _vp, _vp, _vp, _sz, _sz, _sz, _vp]),
     "icm_ctx_set_variant": (_i32, [_vp, _i32]),
     "icm_device_status": (_i32, [_i32]),
     "icm_match_host_workspace_bytes": (_i32, [_vp, _vp, _sz, _i32, ctypes.POINTER(_sz)]),
@@ -364,6 +365,12 @@ def icm_server_stats(srv):
 
 def icm_server_destroy(srv, timeout_ms=600000):
     _check(lib().icm_server_destroy(srv, timeout_ms), "icm_server_destroy")
+
+
+def icm_ppmm_noalloc(form, q, n_limbs, dev_A, dev_B, dev_C, M, N, K, stream=None):
+    qa = (ctypes.c_uint64 * n_limbs)(*[int(x) for x in q[:n_limbs]])
+    _check(lib().icm_ppmm_noalloc(form, qa, n_limbs, _ptr(dev_A), _ptr(dev_B), _ptr(dev_C), M, N, K, _stream(stream)),
+           "icm_ppmm_noalloc")
 
 
 def icm_sync(stream=None, timeout_ms: int = 600000):
