@@ -28,16 +28,20 @@
 
 namespace {
 
-constexpr int BM = 128, BN = 256, KS = 32, S = 4, FLUSH_SLABS = 16;
+constexpr int BM = 128, BN = 256, KS = 32, S = 5, FLUSH_SLABS = 16;
+constexpr int D = 2;                             // raw database slabs prefetched ahead (cp.async)
+constexpr int RS = D + 1;                        // raw slab stages
+constexpr int LAG = S - D;                       // accumulator reductions trail production by LAG slabs
 constexpr int NCONV = 256;                       // converter threads (8 warps)
 constexpr int NT = NCONV + 32;                   // + MMA warp
 constexpr int A_STAGE = BM * KS * 2;             // 8 KB
 constexpr int B_STAGE = BN * KS * 2;             // 16 KB
+constexpr int RAW_STAGE = BM * KS * 8;           // 32 KB of balanced-digit words
 constexpr uint32_t TMEM_COLS = 256;
 constexpr uint64_t WAIT_NS = 2000000000ull;      // bound of every wait
 // Shared memory: ring, mbarriers, TMEM address, abort flag.  The block opts in to the full
 // 227 KB so that descriptor offsets stay inside its allocation under any stride reading.
-constexpr int SMEM_RING = S * (A_STAGE + B_STAGE);
+constexpr int SMEM_RING = S * (A_STAGE + B_STAGE) + RS * RAW_STAGE;
 constexpr int SMEM_BYTES = 227 * 1024;
 constexpr uint64_t NCHUNK = 512;
 
@@ -159,6 +163,7 @@ __global__ void __launch_bounds__(NT, 1) k_crt_tc(TcArgs p) {
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char *sA = smem;                          // [S][A_STAGE]
     unsigned char *sB = smem + S * A_STAGE;            // [S][B_STAGE]
+    unsigned char *sR = smem + S * (A_STAGE + B_STAGE); // [RS][RAW_STAGE]: raw slabs, per-thread chunks
     Bars *bars = reinterpret_cast<Bars *>(smem + SMEM_RING);
     volatile int *abort_flag = &bars->abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -254,17 +259,27 @@ __global__ void __launch_bounds__(NT, 1) k_crt_tc(TcArgs p) {
             };
             auto is_flush = [&](uint64_t f) { return ((f + 1) % FLUSH_SLABS) == 0 && f + 1 < nk; };
 
-            bool alive = true;
-            for (uint64_t kt = 0; kt < nk && alive; ++kt, ++g) {
-                const uint32_t s = (uint32_t)(g % S);
-                const uint32_t u = (uint32_t)(g / S);
+            // loads of slab kk (ring position gg): the raw database words of this thread's two
+            // chunks into its raw stage, and the query planes of the slab into the ring stage
+            auto issue = [&](uint64_t kk, uint64_t gg) -> bool {
+                const uint32_t s = (uint32_t)(gg % S), u = (uint32_t)(gg / S);
                 if (u > 0 && !__all_sync(0xffffffffu, mbar_wait(&bars->empty[s], (u - 1) & 1, abort_flag))) {
                     *abort_flag = 1;
-                    break;
+                    return false;
                 }
-                const uint64_t k0 = kt * KS;
-                unsigned char *a_s = sA + s * A_STAGE, *b_s = sB + s * B_STAGE;
-                // B: 256 columns x 4 chunks of 8 halves
+                const uint64_t k0 = kk * KS;
+                unsigned char *r_s = sR + (gg % RS) * RAW_STAGE, *b_s = sB + s * B_STAGE;
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int id = tid + e * NCONV, row = id >> 2, j = id & 3;
+                    const uint64_t grow = m0 + row, kk8 = k0 + 8 * j;
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+                        const bool ok = grow < M && kk8 + 2 * h < K;        // K is even: whole pair in range
+                        const uint64_t *src = ok ? Al + grow * K + kk8 + 2 * h : Al;
+                        cp_async16(smem_u32(r_s + id * 64 + h * 16), src, ok);
+                    }
+                }
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     const int id = tid + e * NCONV, n = id >> 2, j = id & 3;
@@ -273,35 +288,47 @@ __global__ void __launch_bounds__(NT, 1) k_crt_tc(TcArgs p) {
                     cp_async16(smem_u32(b_s + (j * 32 + (n >> 3)) * 128 + (n & 7) * 16), src, ok);
                 }
                 asm volatile("cp.async.commit_group;" ::: "memory");
-                // A: 128 rows x 4 chunks of 8 residues, two chunks per thread
+                return true;
+            };
+
+            bool alive = true;
+            for (uint64_t d = 0; d < (uint64_t)D && d < nk && alive; ++d) alive = issue(d, g + d);
+            for (uint64_t kt = 0; kt < nk && alive; ++kt) {
+                const uint64_t gg = g + kt;
+                const uint32_t s = (uint32_t)(gg % S);
+                if (kt + D < nk && !issue(kt + D, gg + D)) break;
+                // slab kt's copies have landed once at most min(D, nk - 1 - kt) later groups are pending
+                const uint64_t later = (nk - 1 - kt) < (uint64_t)D ? (nk - 1 - kt) : (uint64_t)D;
+                if (later >= 2) asm volatile("cp.async.wait_group 2;" ::: "memory");
+                else if (later == 1) asm volatile("cp.async.wait_group 1;" ::: "memory");
+                else asm volatile("cp.async.wait_group 0;" ::: "memory");
+                // convert this thread's raw chunks into fp16 residues in the ring stage
+                const unsigned char *r_s = sR + (gg % RS) * RAW_STAGE;
+                unsigned char *a_s = sA + s * A_STAGE;
 #pragma unroll
                 for (int e = 0; e < 2; ++e) {
                     const int id = tid + e * NCONV, row = id >> 2, j = id & 3;
-                    const uint64_t grow = m0 + row, kk = k0 + 8 * j;
                     uint32_t w[4];
 #pragma unroll
                     for (int h = 0; h < 4; ++h) {
-                        uint64_t z0 = 0, z1 = 0;
-                        if (grow < M && kk + 2 * h < K) {        // K is even: the pair is in range and 16-byte aligned
-                            const ulonglong2 zz = __ldg(reinterpret_cast<const ulonglong2 *>(Al + grow * K + kk + 2 * h));
-                            z0 = zz.x;
-                            z1 = zz.y;
-                        }
-                        w[h] = res_half(z0, m, wlo, whi, inv_m) | (res_half(z1, m, wlo, whi, inv_m) << 16);
+                        const ulonglong2 zz = *reinterpret_cast<const ulonglong2 *>(r_s + id * 64 + h * 16);
+                        w[h] = res_half(zz.x, m, wlo, whi, inv_m) | (res_half(zz.y, m, wlo, whi, inv_m) << 16);
                     }
                     *reinterpret_cast<uint4 *>(a_s + (j * 16 + (row >> 3)) * 128 + (row & 7) * 16) = make_uint4(w[0], w[1], w[2], w[3]);
                 }
-                asm volatile("cp.async.wait_group 0;" ::: "memory");
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 mbar_arrive(&bars->full[s]);
-                // reductions lag S - 1 slabs behind production
-                if (kt >= S - 1 && is_flush(kt - (S - 1))) drain(false);
+                // reductions trail production by LAG slabs (the ring can run LAG slabs past a
+                // reduction point before a load would wait on the blocked MMA thread)
+                if (kt >= (uint64_t)LAG && is_flush(kt - LAG)) drain(false);
                 alive = go();
             }
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
             // remaining reductions, then the final residues of the tile
-            for (uint64_t f = (nk >= S - 1 ? nk - (S - 1) : 0); f < nk && go(); ++f)
+            for (uint64_t f = (nk >= (uint64_t)LAG ? nk - LAG : 0); f < nk && go(); ++f)
                 if (is_flush(f)) drain(false);
             if (go()) drain(true);
+            g += nk;
         }
     } else if (lane == 0) {
         // ------------------------------------------------------------------ MMA warp (one thread)

@@ -17,6 +17,7 @@ import torch
 
 from . import build as B
 from . import engine as E
+from . import icm as C
 from . import synth
 
 WORKLOADS = {
@@ -31,11 +32,15 @@ def main(argv=None):
     ap.add_argument("--workload", default="tiny", choices=sorted(WORKLOADS))
     ap.add_argument("--form", default="f16_crt", choices=["u64", "i8_digits", "i8_crt", "f16_crt"])
     ap.add_argument("--passes", type=int, default=1)
+    ap.add_argument("--variant", type=int, default=None,
+                    help="CRT product kernel: 1 = tcgen05, 128 / 256 = mma.sync column tile (default: library's)")
     a = ap.parse_args(argv)
     B.build()
     params, wl = WORKLOADS[a.workload]
     W = synth.make_workload(**wl)
     eng = E.Engine(**params).keygen()
+    if a.variant is not None:
+        C.icm_ctx_set_variant(eng.ctx, a.variant)
     db = eng.encrypt_db(W.db_codes, W.db_masks)
     ct = eng.encrypt_query(W.q_codes, W.q_masks, W.eye_ids)
     torch.cuda.synchronize()
