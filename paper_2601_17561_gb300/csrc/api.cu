@@ -59,10 +59,10 @@ LimbTable make_limb_table(const std::vector<uint64_t> &q) {
     for (size_t l = 0; l < q.size(); ++l) {
         t.q[l] = q[l];
         t.r64[l] = (uint64_t)(((u128)1 << 64) / q[l]);            // floor(2^64 / q), q >= 3
-        for (int s = 0; s < 5; ++s) {
-            t.pw20[l][s] = powmod(2, 20ull * s, q[l]);
-            t.pw20s[l][s] = shoup_of(t.pw20[l][s], q[l]);
-        }
+        t.pw64[l] = powmod(2, 64, q[l]);
+        t.pw64s[l] = shoup_of(t.pw64[l], q[l]);
+        t.pw128[l] = powmod(2, 128, q[l]);
+        t.pw128s[l] = shoup_of(t.pw128[l], q[l]);
     }
     return t;
 }
@@ -147,7 +147,7 @@ icm_status icm_ctx_create(const icm_params *p, icm_ctx **out) {
     if (P.noise_eta == 0 || P.noise_eta > 32) return fail(ICM_EINVAL, "noise_eta must be 1..32");
     if (P.log2_delta == 0 || P.log2_delta > 120) return fail(ICM_EINVAL, "log2_delta must be 1..120");
     const uint64_t K = (uint64_t)P.d2 + Nq;
-    if (3 * K >= (1ull << 24)) return fail(ICM_EUNSUPPORTED, "K too large for the exact u64 accumulation");
+    if (K >= (1ull << 32)) return fail(ICM_EUNSUPPORTED, "K too large");
 
     std::vector<uint64_t> q = pick_primes(P.prime_bits, P.n_limbs);
     if (q.size() != P.n_limbs) return fail(ICM_EINVAL, "not enough primes");
@@ -549,7 +549,7 @@ icm_status icm_ppmm(icm_form form, const uint64_t *q, uint32_t n_limbs, const ui
     if (n_limbs < 1 || n_limbs > ICM_MAX_LIMBS) return fail(ICM_EINVAL, "n_limbs must be 1..8");
     for (uint32_t l = 0; l < n_limbs; ++l)
         if (q[l] < 3 || q[l] >= (1ull << 60) || !(q[l] & 1)) return fail(ICM_EINVAL, "moduli must be odd and below 2^60");
-    if (3 * (uint64_t)K >= (1ull << 24)) return fail(ICM_EBOUND, "K too large for exact accumulation");
+    if ((uint64_t)K >= (1ull << 32)) return fail(ICM_EBOUND, "K too large for exact accumulation");
     std::vector<uint64_t> qv(q, q + n_limbs);
     const LimbTable lt = make_limb_table(qv);
     if (crt_set_attributes() != cudaSuccess) return fail(ICM_ECUDA, "kernel attributes");

@@ -15,8 +15,8 @@ struct LimbTable {
     uint32_t n;                          // number of limbs
     uint64_t q[ICM_MAX_LIMBS];           // primes
     uint64_t r64[ICM_MAX_LIMBS];         // floor(2^64 / q)
-    uint64_t pw20[ICM_MAX_LIMBS][5];     // 2^(20 i) mod q      (u64 GEMM recombination)
-    uint64_t pw20s[ICM_MAX_LIMBS][5];    // Shoup companions floor(w 2^64 / q)
+    uint64_t pw64[ICM_MAX_LIMBS], pw64s[ICM_MAX_LIMBS];     // 2^64 mod q and Shoup companion
+    uint64_t pw128[ICM_MAX_LIMBS], pw128s[ICM_MAX_LIMBS];   // 2^128 mod q and Shoup companion
 };
 
 __host__ __device__ __forceinline__ uint64_t sm_mix64(uint64_t z) {
