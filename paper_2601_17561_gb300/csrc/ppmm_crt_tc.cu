@@ -1,58 +1,80 @@
 // Phase 1 of the fp16 small-modulus CRT product on the tcgen05 tensor cores (Blackwell 5th-gen
 // MMA with accumulators in tensor memory).  Same arithmetic as k_crt_p1<fp16> (ppmm_crt.cu):
 // for one (limb, database chunk, 128-row tile, modulus m_i, 256-column tile) it computes
-// c_i = (sum_k a[k] b[k]) mod m_i over centred residues held exactly in fp16, accumulating in fp32
-// TMEM and reducing the accumulator modulo m_i every 512 columns of K so that it stays an exact
-// integer below 2^24; c_i goes to the byte scratch that phase 2 (k_crt_combine) recombines.
+// c_i = (sum_k a[k] b[k]) mod m_i over residues held exactly in fp16 (|r| <= 128), accumulating
+// in fp32 TMEM and reducing the accumulator modulo m_i every 512 columns of K so that it stays an
+// exact integer below 2^24; c_i goes to the byte scratch that phase 2 (k_crt_combine) recombines.
 //
-// Block: 8 converter warps + 1 MMA warp.  A 4-stage ring in shared memory holds, per K-slab of 32,
-//   A: 128 x 32 fp16 residues of the database rows (converted from the balanced-digit storage
-//      words by the converter warps: two dp4a and one rounding step per residue),
-//   B: 256 x 32 fp16 residue planes of the query (copied with cp.async),
-// both in the K-major canonical layout without swizzle (8-row x 16-byte core matrices; LBO = byte
-// step between core matrices along K, SBO = step between 8-row groups).  One elected thread of the
-// MMA warp issues two tcgen05.mma (M = 128, N = 256, K = 16) per slab into a 256-column fp32 TMEM
-// accumulator and commits to the stage's "empty" mbarrier.  Every 16 slabs, and at the end of a
-// tile, it commits to "acc_full"; the converter warps (two per TMEM lane quarter, 128 columns
-// each) then reduce the accumulator in place (tcgen05.ld / st) or write the final residues, and
-// arrive on "acc_free".  The converters run S - 1 slabs ahead of the reductions, so the ring is
-// full when the MMA thread resumes.
+// Block: 8 converter warps, 1 MMA warp, 2 TMA producer warps; K advances in slabs of 16.
+//  * Raw producer: one TMA load per slab of the 128 x 16 balanced-digit storage words of the
+//    database rows (128-byte swizzle: the 16-byte chunk c of row r sits at chunk c ^ (r mod 8)),
+//    into a ring of RS raw stages ("rawfull" / "rawempty" mbarriers).
+//  * Query producer: one TMA load per slab of the 256 x 16 fp16 residue planes of the query
+//    (32-byte swizzle, the canonical K-major SW32 layout of the MMA) into the B half of a ring of
+//    S operand stages ("bfull"; released by the MMA through "empty").
+//  * Converters: each thread turns 8 consecutive storage words of one row into 8 fp16 residues
+//    (two dp4a, a multiply-high division and an f16x2 add per pair; no conversion-pipe
+//    instructions) and writes them to the A half of the operand stage (K-major, no swizzle,
+//    8-row x 16-byte core matrices).  The thread-to-(row, k-group) map makes every quarter-warp
+//    read 8 distinct bank groups of the swizzled raw stage and write 128 contiguous bytes.
+//  * MMA: one elected thread issues tcgen05.mma (M = 128, N = 256, K = 16) per slab into a
+//    256-column fp32 accumulator and commits to the stage's "empty" mbarrier.  Every 32 slabs and
+//    at the end of a tile it commits to "acc_full"; the converters (two per TMEM lane quarter, 128
+//    columns each) reduce the accumulator in place (tcgen05.ld / st) or write the final residues,
+//    and arrive on "acc_free".  Reductions trail conversion by LAG slabs so that the MMA thread
+//    resumes with LAG converted slabs queued.
 //
 // Every wait is bounded by %globaltimer (2 s); on expiry the block records ICM_DEV_TIMEOUT in the
-// device status word, stops issuing work, waits (bounded) for its own MMAs and frees its TMEM.
+// device status word, stops issuing work, waits (bounded) for its own MMAs and TMA loads, and
+// frees its TMEM.
 #include "icm_internal.h"
 #include "ppmm_i8.h"
 
 #include <algorithm>
+#include <cuda.h>
 #include <cuda_fp16.h>
+#include <mutex>
 
 namespace {
 
-constexpr int BM = 128, BN = 256, KS = 32, S = 5, FLUSH_SLABS = 16;
-constexpr int D = 2;                             // raw database slabs prefetched ahead (cp.async)
-constexpr int RS = D + 1;                        // raw slab stages
-constexpr int LAG = S - D;                       // accumulator reductions trail production by LAG slabs
-constexpr int NCONV = 256;                       // converter threads (8 warps)
-constexpr int NT = NCONV + 32;                   // + MMA warp
-constexpr int A_STAGE = BM * KS * 2;             // 8 KB
-constexpr int B_STAGE = BN * KS * 2;             // 16 KB
-constexpr int RAW_STAGE = BM * KS * 8;           // 32 KB of balanced-digit words
+constexpr int BM = 128, BN = 256, KS = 16;
+constexpr int S = 8;                              // operand stages (A residues + B planes)
+constexpr int RS = 7;                             // raw database stages
+constexpr int FLUSH_SLABS = 32;                   // 512 columns of K between reductions
+constexpr int LAG = S - 2;                        // reductions trail conversion by LAG slabs
+constexpr int NCONV = 256;                        // converter threads (8 warps)
+constexpr int W_MMA = NCONV / 32, W_RAW = W_MMA + 1, W_QRY = W_MMA + 2;
+constexpr int NT = NCONV + 96;                    // + MMA warp + two producer warps
+constexpr int A_STAGE = BM * KS * 2;              // 4 KB
+constexpr int B_STAGE = BN * KS * 2;              // 8 KB
+constexpr int RAW_STAGE = BM * KS * 8;            // 16 KB
 constexpr uint32_t TMEM_COLS = 256;
-constexpr uint64_t WAIT_NS = 2000000000ull;      // bound of every wait
-// Shared memory: ring, mbarriers, TMEM address, abort flag.  The block opts in to the full
-// 227 KB so that descriptor offsets stay inside its allocation under any stride reading.
-constexpr int SMEM_RING = S * (A_STAGE + B_STAGE) + RS * RAW_STAGE;
-constexpr int SMEM_BYTES = 227 * 1024;
+constexpr uint64_t WAIT_NS = 2000000000ull;       // bound of every wait
+// Shared memory: raw stages first (1024-byte aligned for the 128-byte swizzle), then B and A
+// stages, then the mbarriers.
+constexpr int OFF_B = RS * RAW_STAGE;
+constexpr int OFF_A = OFF_B + S * B_STAGE;
+constexpr int SMEM_RING = OFF_A + S * A_STAGE;
+constexpr int SMEM_BYTES = SMEM_RING + 2048;      // + barriers + slack to align the base to 1024
+static_assert(SMEM_BYTES <= 227 * 1024, "shared memory budget");
+static_assert(OFF_B % 1024 == 0 && OFF_A % 1024 == 0, "stage alignment");
 constexpr uint64_t NCHUNK = 512;
 
+struct TcMod {
+    int32_t m, wlo, whi, cbias;
+    uint32_t magic, hneg2;
+    float inv_m;
+};
+
 struct TcArgs {
+    CUtensorMap tmA[ICM_MAX_CHUNKS];  // per chunk: [L][M_c][K] u64, box 16 x 128, 128-byte swizzle
+    CUtensorMap tmB;                  // [L][r][N][Kp] fp16, box 16 x 256, 32-byte swizzle
     icm::ChunkTab tab;
-    const void *Bp;          // [L][r][N][Kp] fp16 planes
-    uint8_t *R;              // [L][r][nch][sum M_c]
-    uint64_t N, K, Kp, n0, nch;
-    uint32_t n_ntile;
+    uint8_t *R;                       // [L][r][nch][sum M_c]
+    uint64_t N, K, n0, nch;
+    uint32_t n_ntile, n_mod;
     uint64_t n_tiles;
-    icm::I8Consts k;
+    TcMod md[ICM_MAX_MODULI];
 };
 
 // Device status word: ICM_DEV_TIMEOUT once any block gave up a bounded wait (read and cleared by
@@ -71,6 +93,10 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
 }
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" :: "r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}"
+                 :: "r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
@@ -92,16 +118,38 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volati
         }
     }
 }
+// Bounded wait that ignores the abort flag (drains this block's own copies before it exits).
+__device__ __forceinline__ void mbar_wait_drain(uint64_t *bar, uint32_t parity) {
+    const uint64_t t0 = gtime();
+    while (!mbar_try(bar, parity))
+        if (gtime() - t0 > WAIT_NS) {
+            atomicExch(&g_status, (uint32_t)ICM_DEV_TIMEOUT);
+            return;
+        }
+}
+
+// TMA tile loads into this block's shared memory, completing on an mbarrier.
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, uint64_t *bar) {
+    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+                 :: "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                            uint64_t *bar) {
+    asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+                 :: "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+                 : "memory");
+}
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// K-major canonical layout without swizzle: descriptor fields (bits): start address >> 4 [0,14),
-// leading byte offset >> 4 [16,30), stride byte offset >> 4 [32,46), version 1 [46,48),
-// base offset 0, layout type 0 (no swizzle) [61,64).
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+// Shared memory matrix descriptor: start address >> 4 [0,14), leading byte offset >> 4 [16,30),
+// stride byte offset >> 4 [32,46), version 1 [46,48), base offset 0, swizzle mode [61,64)
+// (0 none, 6 32-byte).
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo, uint32_t swz) {
     return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | ((uint64_t)swz << 61);
 }
 // Instruction descriptor, kind::f16: D = f32 [4,6), A = B = f16 [7,10) [10,13), both K-major,
 // N >> 3 [17,23), M >> 4 [24,29).
@@ -141,35 +189,67 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32
                  : "memory");
 }
 
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, bool pred) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" :: "r"(dst), "l"(src), "r"(pred ? 16 : 0) : "memory");
-}
-
-// centred residue of a balanced-digit storage word modulo m (|r| <= m/2), as fp16 bits
-__device__ __forceinline__ uint32_t res_half(uint64_t z, int m, int wlo, int whi, float inv_m) {
-    int s = __dp4a((int)(uint32_t)z, wlo, 0);
-    s = __dp4a((int)(uint32_t)(z >> 32), whi, s);
-    const int r = s - m * __float2int_rn((float)s * inv_m);
-    return (uint32_t)__half_as_ushort(__int2half_rn(r));
+// Residues modulo m of two balanced-digit storage words, as f16x2 bits, in integer arithmetic:
+// v = sum_t d_t (256^t mod m) + c lies in [0, 2^19) (|sum| <= 2^17, c = m ceil(2^17 / m) + h),
+// x = v - m floor(v / m) in [0, m) with the quotient from one multiply-high by ceil(2^32 / m)
+// (exact because v (ceil(2^32/m) m - 2^32) < 2^32), so x - h = sum mod m with |x - h| <= 128.
+// The f16 bits of 1024 + x are 0x6400 + x, and one f16x2 add of -(1024 + h) leaves x - h exactly.
+__device__ __forceinline__ uint32_t res_pair(uint64_t z0, uint64_t z1, int wlo, int whi, int cb, uint32_t magic,
+                                             uint32_t m, uint32_t hneg2) {
+    const uint32_t v0 = (uint32_t)__dp4a((int)(uint32_t)(z0 >> 32), whi, __dp4a((int)(uint32_t)z0, wlo, cb));
+    const uint32_t v1 = (uint32_t)__dp4a((int)(uint32_t)(z1 >> 32), whi, __dp4a((int)(uint32_t)z1, wlo, cb));
+    const uint32_t x0 = v0 - __umulhi(v0, magic) * m, x1 = v1 - __umulhi(v1, magic) * m;
+    const uint32_t bits = __byte_perm(x0, x1, 0x5410) + 0x64006400u;
+    uint32_t out;
+    asm("add.rn.f16x2 %0, %1, %2;" : "=r"(out) : "r"(bits), "r"(hneg2));
+    return out;
 }
 
 struct __align__(8) Bars {
-    uint64_t full[S], empty[S], acc_full, acc_free, done;
+    uint64_t rawfull[RS], rawempty[RS], full[S], bfull[S], empty[S], acc_full, acc_free, done;
     uint32_t tmem;
     int abort_flag;
 };
+static_assert(sizeof(Bars) <= 1024, "barrier block");
 
-__global__ void __launch_bounds__(NT, 1) k_crt_tc(TcArgs p) {
-    extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char *sA = smem;                          // [S][A_STAGE]
-    unsigned char *sB = smem + S * A_STAGE;            // [S][B_STAGE]
-    unsigned char *sR = smem + S * (A_STAGE + B_STAGE); // [RS][RAW_STAGE]: raw slabs, per-thread chunks
+struct TileCoord {
+    uint32_t l, c, mi, nt;
+    uint64_t m0, M;
+};
+__device__ __forceinline__ TileCoord tile_coord(const TcArgs &p, uint64_t tile) {
+    TileCoord t;
+    uint64_t tt = tile;
+    t.nt = (uint32_t)(tt % p.n_ntile); tt /= p.n_ntile;
+    t.mi = (uint32_t)(tt % p.n_mod); tt /= p.n_mod;
+    const uint32_t mt_total = p.tab.mt0[p.tab.n];
+    const uint32_t mtg = (uint32_t)(tt % mt_total);
+    t.l = (uint32_t)(tt / mt_total);
+    uint32_t c = 0;
+    while (c + 1 < p.tab.n && mtg >= p.tab.mt0[c + 1]) ++c;
+    t.c = c;
+    t.M = p.tab.M[c];
+    t.m0 = (uint64_t)(mtg - p.tab.mt0[c]) * BM;
+    return t;
+}
+
+__global__ void __launch_bounds__(NT, 1) k_crt_tc(const __grid_constant__ TcArgs p) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // the swizzle patterns are functions of shared-memory address bits: align the base to 1024
+    unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    unsigned char *sR = smem;                          // [RS][RAW_STAGE]
+    unsigned char *sB = smem + OFF_B;                  // [S][B_STAGE]
+    unsigned char *sA = smem + OFF_A;                  // [S][A_STAGE]
     Bars *bars = reinterpret_cast<Bars *>(smem + SMEM_RING);
     volatile int *abort_flag = &bars->abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     if (tid == 0) {
-        for (int s = 0; s < S; ++s) { mbar_init(&bars->full[s], NCONV); mbar_init(&bars->empty[s], 1); }
+        for (int s = 0; s < RS; ++s) { mbar_init(&bars->rawfull[s], 1); mbar_init(&bars->rawempty[s], NCONV); }
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&bars->full[s], NCONV);
+            mbar_init(&bars->bfull[s], 1);
+            mbar_init(&bars->empty[s], 1);
+        }
         mbar_init(&bars->acc_full, 1);
         mbar_init(&bars->acc_free, NCONV);
         mbar_init(&bars->done, 1);
@@ -186,39 +266,33 @@ __global__ void __launch_bounds__(NT, 1) k_crt_tc(TcArgs p) {
     tc_fence_after();
     const uint32_t tmem = bars->tmem;
 
-    const uint32_t r = p.k.n_mod;
-    const uint32_t mt_total = p.tab.mt0[p.tab.n];
-    const uint64_t N = p.N, K = p.K, Kp = p.Kp;
+    const uint64_t K = p.K, N = p.N;
     const uint64_t nk = (K + KS - 1) / KS;
     const uint64_t Mall = p.tab.row0[p.tab.n];
+    auto is_flush = [&](uint64_t f) { return ((f + 1) % FLUSH_SLABS) == 0 && f + 1 < nk; };
 
-    if (warp < NCONV / 32) {
+    if (warp < W_MMA) {
         // ------------------------------------------------------------------ converter warps
         uint64_t g = 0;                 // global slab counter (ring position)
         uint32_t acc_uses = 0;          // acc_full completions consumed
         const uint32_t qtr = warp & 3, half = warp >> 2;                 // TMEM lane quarter, column half
         const uint32_t trow = qtr * 32 + lane;                           // accumulator row of this thread
+        // conversion map: row and k-group (8 columns) of this thread within the slab
+        const uint32_t crow = (uint32_t)warp * 16 + ((uint32_t)(lane >> 4) << 3) + (lane & 7);
+        const uint32_t cj = (lane >> 3) & 1;
+        const uint32_t rsw = crow & 7;
+        const uint32_t a_off = (cj * 16 + (crow >> 3)) * 128 + (crow & 7) * 16;
         // every loop decision below is warp-uniform (__all_sync), because drain() issues
         // warp-collective TMEM instructions
         auto go = [&]() { return __all_sync(0xffffffffu, *abort_flag == 0); };
         for (uint64_t tile = blockIdx.x; tile < p.n_tiles && go(); tile += gridDim.x) {
-            uint64_t tt = tile;
-            const uint32_t nt = (uint32_t)(tt % p.n_ntile); tt /= p.n_ntile;
-            const uint32_t mi = (uint32_t)(tt % r); tt /= r;
-            const uint32_t mtg = (uint32_t)(tt % mt_total);
-            const uint32_t l = (uint32_t)(tt / mt_total);
-            uint32_t c = 0;
-            while (c + 1 < p.tab.n && mtg >= p.tab.mt0[c + 1]) ++c;
-            const uint64_t M = p.tab.M[c];
-            const uint64_t m0 = (uint64_t)(mtg - p.tab.mt0[c]) * BM, nb = (uint64_t)nt * BN;
-            const int m = p.k.mod[mi], wlo = p.k.wlo[mi], whi = p.k.whi[mi];
-            const float inv_m = p.k.inv_m[mi], fm = (float)m;
-            const uint64_t *Al = p.tab.A[c] + (size_t)l * M * K;
-            const unsigned char *Bl = reinterpret_cast<const unsigned char *>(p.Bp) + (((size_t)l * r + mi) * N + p.n0) * Kp * 2;
+            const TileCoord tc = tile_coord(p, tile);
+            const TcMod md = p.md[tc.mi];
+            const uint64_t nb = (uint64_t)tc.nt * BN;
+            const float fm = (float)md.m;
 
             // the reduction (or final write) of the accumulator after slab f
             auto drain = [&](bool final) {
-                // warp-uniform decision: the TMEM loads and stores below are warp-collective
                 const bool ok = __all_sync(0xffffffffu, mbar_wait(&bars->acc_full, acc_uses & 1, abort_flag));
                 if (!ok) {
                     *abort_flag = 1;
@@ -232,22 +306,24 @@ __global__ void __launch_bounds__(NT, 1) k_crt_tc(TcArgs p) {
                     uint32_t v[32];
                     tmem_ld32(taddr, v);
                     if (!final) {
+                        // x - m round(x / m): the fma adds 1.5 2^23 to the exact x / m estimate
+                        // and rounds once, which rounds it to an integer (|x / m| < 2^22)
 #pragma unroll
                         for (int j = 0; j < 32; ++j) {
-                            float x = __uint_as_float(v[j]);
-                            x = fmaf(-fm, rintf(x * inv_m), x);
-                            v[j] = __float_as_uint(x);
+                            const float x = __uint_as_float(v[j]);
+                            const float t = __fsub_rn(fmaf(x, md.inv_m, 12582912.0f), 12582912.0f);
+                            v[j] = __float_as_uint(fmaf(-fm, t, x));
                         }
                         tmem_st32(taddr, v);
                     } else {
-                        const uint64_t row = m0 + trow;
-                        uint8_t *Rl = p.R + ((size_t)l * r + mi) * p.nch * Mall + p.tab.row0[c];
-#pragma unroll 4
+                        const uint64_t row = tc.m0 + trow;
+                        uint8_t *Rl = p.R + ((size_t)tc.l * p.n_mod + tc.mi) * p.nch * Mall + p.tab.row0[tc.c];
+#pragma unroll
                         for (int j = 0; j < 32; ++j) {
                             const uint64_t col = nb + col0 + j;
-                            if (row < M && col < p.nch && p.n0 + col < N) {
-                                int val = __float2int_rn(__uint_as_float(v[j])) % m;
-                                val = val < 0 ? val + m : val;
+                            if (row < tc.M && col < p.nch && p.n0 + col < N) {
+                                int val = __float2int_rn(__uint_as_float(v[j])) % md.m;
+                                val = val < 0 ? val + md.m : val;
                                 Rl[col * Mall + row] = (uint8_t)val;
                             }
                         }
@@ -257,81 +333,40 @@ __global__ void __launch_bounds__(NT, 1) k_crt_tc(TcArgs p) {
                 tc_fence_before();
                 mbar_arrive(&bars->acc_free);
             };
-            auto is_flush = [&](uint64_t f) { return ((f + 1) % FLUSH_SLABS) == 0 && f + 1 < nk; };
 
-            // loads of slab kk (ring position gg): the raw database words of this thread's two
-            // chunks into its raw stage, and the query planes of the slab into the ring stage
-            auto issue = [&](uint64_t kk, uint64_t gg) -> bool {
-                const uint32_t s = (uint32_t)(gg % S), u = (uint32_t)(gg / S);
-                if (u > 0 && !__all_sync(0xffffffffu, mbar_wait(&bars->empty[s], (u - 1) & 1, abort_flag))) {
-                    *abort_flag = 1;
-                    return false;
-                }
-                const uint64_t k0 = kk * KS;
-                unsigned char *r_s = sR + (gg % RS) * RAW_STAGE, *b_s = sB + s * B_STAGE;
-#pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    const int id = tid + e * NCONV, row = id >> 2, j = id & 3;
-                    const uint64_t grow = m0 + row, kk8 = k0 + 8 * j;
-#pragma unroll
-                    for (int h = 0; h < 4; ++h) {
-                        const bool ok = grow < M && kk8 + 2 * h < K;        // K is even: whole pair in range
-                        const uint64_t *src = ok ? Al + grow * K + kk8 + 2 * h : Al;
-                        cp_async16(smem_u32(r_s + id * 64 + h * 16), src, ok);
-                    }
-                }
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int id = tid + e * NCONV, n = id >> 2, j = id & 3;
-                    const bool ok = nb + n < p.nch && p.n0 + nb + n < N;
-                    const unsigned char *src = Bl + (ok ? ((nb + n) * Kp + k0 + 8 * j) * 2 : 0);
-                    cp_async16(smem_u32(b_s + (j * 32 + (n >> 3)) * 128 + (n & 7) * 16), src, ok);
-                }
-                asm volatile("cp.async.commit_group;" ::: "memory");
-                return true;
-            };
-
-            bool alive = true;
-            for (uint64_t d = 0; d < (uint64_t)D && d < nk && alive; ++d) alive = issue(d, g + d);
-            for (uint64_t kt = 0; kt < nk && alive; ++kt) {
+            for (uint64_t kt = 0; kt < nk; ++kt) {
                 const uint64_t gg = g + kt;
-                const uint32_t s = (uint32_t)(gg % S);
-                if (kt + D < nk && !issue(kt + D, gg + D)) break;
-                // slab kt's copies have landed once at most min(D, nk - 1 - kt) later groups are pending
-                const uint64_t later = (nk - 1 - kt) < (uint64_t)D ? (nk - 1 - kt) : (uint64_t)D;
-                if (later >= 2) asm volatile("cp.async.wait_group 2;" ::: "memory");
-                else if (later == 1) asm volatile("cp.async.wait_group 1;" ::: "memory");
-                else asm volatile("cp.async.wait_group 0;" ::: "memory");
-                // convert this thread's raw chunks into fp16 residues in the ring stage
-                const unsigned char *r_s = sR + (gg % RS) * RAW_STAGE;
-                unsigned char *a_s = sA + s * A_STAGE;
-#pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    const int id = tid + e * NCONV, row = id >> 2, j = id & 3;
-                    uint32_t w[4];
-#pragma unroll
-                    for (int h = 0; h < 4; ++h) {
-                        const ulonglong2 zz = *reinterpret_cast<const ulonglong2 *>(r_s + id * 64 + h * 16);
-                        w[h] = res_half(zz.x, m, wlo, whi, inv_m) | (res_half(zz.y, m, wlo, whi, inv_m) << 16);
-                    }
-                    *reinterpret_cast<uint4 *>(a_s + (j * 16 + (row >> 3)) * 128 + (row & 7) * 16) = make_uint4(w[0], w[1], w[2], w[3]);
+                const uint32_t s = (uint32_t)(gg % S), u = (uint32_t)(gg / S);
+                const uint32_t rs = (uint32_t)(gg % RS), ur = (uint32_t)(gg / RS);
+                bool ok = mbar_wait(&bars->rawfull[rs], ur & 1, abort_flag);
+                if (ok && u > 0) ok = mbar_wait(&bars->empty[s], (u - 1) & 1, abort_flag);
+                if (!__all_sync(0xffffffffu, ok)) {
+                    *abort_flag = 1;
+                    break;
                 }
+                // 8 storage words (4 swizzled 16-byte chunks) of row crow -> 8 fp16 residues
+                const unsigned char *r_s = sR + rs * RAW_STAGE + crow * 128;
+                uint32_t w[4];
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const ulonglong2 zz = *reinterpret_cast<const ulonglong2 *>(r_s + (((cj * 4 + h) ^ rsw) << 4));
+                    w[h] = res_pair(zz.x, zz.y, md.wlo, md.whi, md.cbias, md.magic, (uint32_t)md.m, md.hneg2);
+                }
+                mbar_arrive(&bars->rawempty[rs]);
+                *reinterpret_cast<uint4 *>(sA + s * A_STAGE + a_off) = make_uint4(w[0], w[1], w[2], w[3]);
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 mbar_arrive(&bars->full[s]);
-                // reductions trail production by LAG slabs (the ring can run LAG slabs past a
-                // reduction point before a load would wait on the blocked MMA thread)
                 if (kt >= (uint64_t)LAG && is_flush(kt - LAG)) drain(false);
-                alive = go();
+                if (!go()) break;
             }
-            asm volatile("cp.async.wait_group 0;" ::: "memory");
             // remaining reductions, then the final residues of the tile
             for (uint64_t f = (nk >= (uint64_t)LAG ? nk - LAG : 0); f < nk && go(); ++f)
                 if (is_flush(f)) drain(false);
             if (go()) drain(true);
             g += nk;
         }
-    } else if (lane == 0) {
-        // ------------------------------------------------------------------ MMA warp (one thread)
+    } else if (warp == W_MMA && lane == 0) {
+        // ------------------------------------------------------------------ MMA (one thread)
         uint64_t g = 0;
         uint32_t acc_commits = 0;
         bool wait_free = false;
@@ -344,14 +379,12 @@ __global__ void __launch_bounds__(NT, 1) k_crt_tc(TcArgs p) {
                     wait_free = false;
                 }
                 if (!mbar_wait(&bars->full[s], u & 1, abort_flag)) break;
+                if (!mbar_wait(&bars->bfull[s], u & 1, abort_flag)) break;
                 tc_fence_after();
-                const uint32_t a0 = smem_u32(sA + s * A_STAGE), b0 = smem_u32(sB + s * B_STAGE);
-#pragma unroll
-                for (int ks = 0; ks < 2; ++ks)
-                    umma(tmem, sdesc(a0 + ks * 2 * 2048, 2048, 128), sdesc(b0 + ks * 2 * 4096, 4096, 128),
-                         (kt > 0 || ks > 0) ? 1u : 0u);
+                umma(tmem, sdesc(smem_u32(sA + s * A_STAGE), 2048, 128, 0),
+                     sdesc(smem_u32(sB + s * B_STAGE), 16, 256, 6), kt > 0 ? 1u : 0u);
                 umma_commit(&bars->empty[s]);
-                if ((((kt + 1) % FLUSH_SLABS) == 0 && kt + 1 < nk) || kt + 1 == nk) {
+                if (is_flush(kt) || kt + 1 == nk) {
                     umma_commit(&bars->acc_full);
                     ++acc_commits;
                     wait_free = true;
@@ -360,13 +393,69 @@ __global__ void __launch_bounds__(NT, 1) k_crt_tc(TcArgs p) {
         }
         // make sure every MMA issued by this thread has completed before TMEM is freed
         umma_commit(&bars->done);
-        mbar_wait(&bars->done, 0, abort_flag);
+        mbar_wait_drain(&bars->done, 0);
+    } else if (warp == W_RAW && lane == 0) {
+        // ------------------------------------------------------------------ raw database producer
+        uint64_t g = 0;
+        for (uint64_t tile = blockIdx.x; tile < p.n_tiles && !*abort_flag; tile += gridDim.x) {
+            const TileCoord tc = tile_coord(p, tile);
+            bool alive = true;
+            for (uint64_t kt = 0; kt < nk; ++kt, ++g) {
+                const uint32_t rs = (uint32_t)(g % RS), ur = (uint32_t)(g / RS);
+                if (ur > 0 && !mbar_wait(&bars->rawempty[rs], (ur - 1) & 1, abort_flag)) { alive = false; break; }
+                mbar_expect_tx(&bars->rawfull[rs], RAW_STAGE);
+                tma_load_3d(smem_u32(sR + rs * RAW_STAGE), &p.tmA[tc.c], (int)(kt * KS), (int)tc.m0, (int)tc.l,
+                            &bars->rawfull[rs]);
+            }
+            if (!alive) break;
+        }
+        // every load issued by this thread has landed before the block exits
+        for (uint64_t i = (g > (uint64_t)RS ? g - RS : 0); i < g; ++i)
+            mbar_wait_drain(&bars->rawfull[i % RS], (uint32_t)((i / RS) & 1));
+    } else if (warp == W_QRY && lane == 0) {
+        // ------------------------------------------------------------------ query plane producer
+        uint64_t g = 0;
+        for (uint64_t tile = blockIdx.x; tile < p.n_tiles && !*abort_flag; tile += gridDim.x) {
+            const TileCoord tc = tile_coord(p, tile);
+            const uint64_t nb = (uint64_t)tc.nt * BN;
+            bool alive = true;
+            for (uint64_t kt = 0; kt < nk; ++kt, ++g) {
+                const uint32_t s = (uint32_t)(g % S), u = (uint32_t)(g / S);
+                if (u > 0 && !mbar_wait(&bars->empty[s], (u - 1) & 1, abort_flag)) { alive = false; break; }
+                mbar_expect_tx(&bars->bfull[s], B_STAGE);
+                tma_load_4d(smem_u32(sB + s * B_STAGE), &p.tmB, (int)(kt * KS), (int)(p.n0 + nb), (int)tc.mi, (int)tc.l,
+                            &bars->bfull[s]);
+            }
+            if (!alive) break;
+        }
+        for (uint64_t i = (g > (uint64_t)S ? g - S : 0); i < g; ++i)
+            mbar_wait_drain(&bars->bfull[i % S], (uint32_t)((i / S) & 1));
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+// ---------------------------------------------------------------- host side
+
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link against libcuda).
+EncodeTiled encode_fn() {
+    static std::once_flag once;
+    static EncodeTiled fn = nullptr;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(f);
+    });
+    return fn;
 }
 
 }  // namespace
@@ -377,8 +466,8 @@ cudaError_t crt_tc_set_attributes() {
     return cudaFuncSetAttribute(k_crt_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
 }
 
-// The tcgen05 path needs an even K (16-byte loads of pairs of residues); the caller falls back to
-// the mma.sync kernel otherwise.
+// The tcgen05 path needs an even K (tensor-map row strides are multiples of 16 bytes); the caller
+// uses the mma.sync kernel otherwise.
 bool crt_tc_supported(uint64_t K) { return K > 0 && K % 2 == 0; }
 
 uint32_t device_status(bool clear) {
@@ -395,17 +484,47 @@ cudaError_t launch_ppmm_crt_tc(const I8Consts &k, const ChunkTab &tab, const voi
                                void *scratch, cudaStream_t st) {
     const uint64_t Mall = tab.row0[tab.n];
     if (Mall == 0 || N == 0) return cudaSuccess;
+    if (!crt_tc_supported(K) || Kp % KS) return cudaErrorInvalidValue;
+    EncodeTiled enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+
+    static_assert(sizeof(TcArgs) <= 32000, "kernel parameter space");
+    TcArgs a{};
+    // database chunks: [L][M_c][K] u64, box 16 words x 128 rows x 1 limb
+    for (uint32_t c = 0; c < tab.n; ++c) {
+        const cuuint64_t M = tab.M[c] ? tab.M[c] : 1;
+        const cuuint64_t dims[3] = {K, M, k.n_limbs};
+        const cuuint64_t strides[2] = {K * 8, M * K * 8};
+        const cuuint32_t box[3] = {KS, BM, 1}, estr[3] = {1, 1, 1};
+        if (enc(&a.tmA[c], CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<uint64_t *>(tab.A[c]), dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    // query planes: [L][r][N][Kp] fp16 bits, box 16 columns of K x 256 rows
+    {
+        const cuuint64_t dims[4] = {Kp, N, k.n_mod, k.n_limbs};
+        const cuuint64_t strides[3] = {Kp * 2, N * Kp * 2, (cuuint64_t)k.n_mod * N * Kp * 2};
+        const cuuint32_t box[4] = {KS, BN, 1, 1}, estr[4] = {1, 1, 1, 1};
+        if (enc(&a.tmB, CU_TENSOR_MAP_DATA_TYPE_UINT16, 4, const_cast<void *>(Bp), dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    a.tab = tab;
+    a.R = reinterpret_cast<uint8_t *>(scratch);
+    a.N = N; a.K = K;
+    a.n_mod = k.n_mod;
+    for (uint32_t i = 0; i < k.n_mod; ++i)
+        a.md[i] = TcMod{k.mod[i], k.wlo[i], k.whi[i], k.cbias[i], k.magic[i], k.hneg2[i], k.inv_m[i]};
     for (uint64_t n0 = 0; n0 < N; n0 += NCHUNK) {
         const uint64_t nch = std::min<uint64_t>(NCHUNK, N - n0);
-        TcArgs a{};
-        a.tab = tab; a.Bp = Bp; a.R = reinterpret_cast<uint8_t *>(scratch);
-        a.N = N; a.K = K; a.Kp = Kp; a.n0 = n0; a.nch = nch;
+        a.n0 = n0; a.nch = nch;
         a.n_ntile = (uint32_t)((nch + BN - 1) / BN);
         a.n_tiles = (uint64_t)k.n_limbs * tab.mt0[tab.n] * k.n_mod * a.n_ntile;
-        a.k = k;
         const uint64_t grid = std::min<uint64_t>(a.n_tiles, (uint64_t)sms);
         if (grid == 0) continue;
         k_crt_tc<<<(unsigned)grid, NT, SMEM_BYTES, st>>>(a);

@@ -352,6 +352,11 @@ bool make_i8_consts(int form, const uint64_t *q, size_t nq, uint64_t K, I8Consts
         k.wlo[i] = (int32_t)((uint32_t)(uint8_t)w[0] | ((uint32_t)(uint8_t)w[1] << 8) | ((uint32_t)(uint8_t)w[2] << 16) | ((uint32_t)(uint8_t)w[3] << 24));
         k.whi[i] = (int32_t)((uint32_t)(uint8_t)w[4] | ((uint32_t)(uint8_t)w[5] << 8) | ((uint32_t)(uint8_t)w[6] << 16) | ((uint32_t)(uint8_t)w[7] << 24));
         k.inv_m[i] = 1.0f / (float)m;
+        const int h = m / 2;
+        k.cbias[i] = m * ((131072 + m - 1) / m) + h;
+        k.magic[i] = (uint32_t)(((1ull << 32) + (uint64_t)m - 1) / (uint64_t)m);
+        const uint32_t hb = 0xE400u | (uint32_t)h;           // fp16 bits of -(1024 + h)
+        k.hneg2[i] = hb | (hb << 16);
         // (M / m_i) mod m_i and its inverse
         uint64_t hat = 1;
         for (uint32_t j = 0; j < nm; ++j) if (j != i) hat = hat * (uint64_t)mods[j] % (uint64_t)m;

@@ -19,6 +19,10 @@ struct I8Consts {
     // (M/m_i)^-1 mod m_i, (M/m_i) mod q_l and M mod q_l with Shoup companions
     int32_t mod[ICM_MAX_MODULI], wlo[ICM_MAX_MODULI], whi[ICM_MAX_MODULI], yinv[ICM_MAX_MODULI];
     float inv_m[ICM_MAX_MODULI];
+    // integer residue conversion of the tcgen05 path: dp4a bias c = m ceil(2^17 / m) + h with
+    // h = floor(m / 2), division magic ceil(2^32 / m), and the f16x2 bits of -(1024 + h)
+    int32_t cbias[ICM_MAX_MODULI];
+    uint32_t magic[ICM_MAX_MODULI], hneg2[ICM_MAX_MODULI];
     uint64_t W[ICM_MAX_LIMBS][ICM_MAX_MODULI], Ws[ICM_MAX_LIMBS][ICM_MAX_MODULI];
     uint64_t Mq[ICM_MAX_LIMBS], Mqs[ICM_MAX_LIMBS];
 };

@@ -12,18 +12,21 @@
 // 2^64 mod q_l and 2^128 mod q_l.
 //
 // A arrives either canonical or in the balanced-digit storage form of the database (mapped back to
-// canonical on load).
+// canonical when the slab is stored to shared memory, after the load latency).
 //
 // Tiling: a 64 x 32 output tile per 256-thread block, 4 x 2 outputs per thread (each output holds
-// eleven 32-bit registers of accumulator), K in steps of 16.  Global loads are coalesced along K (both operands are K-contiguous); the tile is split
-// into limbs once on its way into shared memory (stored k-major so that a thread reads its four
-// rows or columns with one 16-byte load per limb); the next K-slab is loaded into registers
+// eleven 32-bit registers of accumulator), K in steps of 16.  Global loads are coalesced along K
+// (both operands are K-contiguous); the tile is split into limbs once on its way into shared
+// memory (stored k-major, rows padded to 2 mod 32 words so that the stores are conflict-free; a
+// thread reads its rows or columns with 8-byte loads); the next K-slab is loaded into registers
 // while the current one is multiplied.
 #include "icm_internal.h"
 
 namespace {
 
-constexpr int BM = 64, BN = 32, BK = 16, PAD = 8, NT = 256, FL = 8, TM = 4, TN = 2;
+constexpr int BM = 64, BN = 32, BK = 16, NT = 256, FL = 8, TM = 4, TN = 2;
+// shared row lengths (words): 2 mod 32 makes the slab stores conflict-free (a warp stores 16 k x 2 rows)
+constexpr int AW = BM + 2, BW = BN + 2;
 
 struct PpmmArgs {
     const uint64_t *A, *B;
@@ -36,8 +39,8 @@ struct PpmmArgs {
 using u128 = unsigned __int128;
 
 __global__ void __launch_bounds__(NT, 1) k_ppmm_u64(PpmmArgs p) {
-    __shared__ __align__(16) uint32_t As[2][BK][BM + PAD];
-    __shared__ __align__(16) uint32_t Bs[2][BK][BN + PAD];
+    __shared__ __align__(16) uint32_t As[2][BK][AW];
+    __shared__ __align__(16) uint32_t Bs[2][BK][BW];
     const uint32_t l = blockIdx.z;
     const uint64_t m0 = (uint64_t)blockIdx.x * BM, n0 = (uint64_t)blockIdx.y * BN;
     const uint64_t M = p.M, N = p.N, K = p.K;
@@ -65,8 +68,7 @@ __global__ void __launch_bounds__(NT, 1) k_ppmm_u64(PpmmArgs p) {
         for (int e = 0; e < BM * BK / NT; ++e) {
             const int idx = tid + e * NT, r = idx >> 4, kk = idx & 15;
             const uint64_t k = k0 + kk;
-            ra[e] = (m0 + r < M && k < K) ? (p.a_digits ? from_digit_form(__ldg(Al + (m0 + r) * K + k), q)
-                                                        : __ldg(Al + (m0 + r) * K + k)) : 0ull;
+            ra[e] = (m0 + r < M && k < K) ? __ldg(Al + (m0 + r) * K + k) : 0ull;
         }
 #pragma unroll
         for (int e = 0; e < BN * BK / NT; ++e) {
@@ -79,8 +81,10 @@ __global__ void __launch_bounds__(NT, 1) k_ppmm_u64(PpmmArgs p) {
 #pragma unroll
         for (int e = 0; e < BM * BK / NT; ++e) {
             const int idx = tid + e * NT, r = idx >> 4, kk = idx & 15;
-            As[0][kk][r] = (uint32_t)(ra[e] & 0x3FFFFFFF);
-            As[1][kk][r] = (uint32_t)(ra[e] >> 30);
+            // digit-form words are mapped back here, after the load latency has passed
+            const uint64_t a = p.a_digits ? from_digit_form(ra[e], q) : ra[e];
+            As[0][kk][r] = (uint32_t)(a & 0x3FFFFFFF);
+            As[1][kk][r] = (uint32_t)(a >> 30);
         }
 #pragma unroll
         for (int e = 0; e < BN * BK / NT; ++e) {
@@ -114,11 +118,13 @@ __global__ void __launch_bounds__(NT, 1) k_ppmm_u64(PpmmArgs p) {
 #pragma unroll
             for (int k8 = 0; k8 < FL; ++k8) {
                 const int kk = half * FL + k8;
-                const uint4 a0 = *reinterpret_cast<const uint4 *>(&As[0][kk][ty * TM]);
-                const uint4 a1 = *reinterpret_cast<const uint4 *>(&As[1][kk][ty * TM]);
+                const uint2 a0l = *reinterpret_cast<const uint2 *>(&As[0][kk][ty * TM]);
+                const uint2 a0h = *reinterpret_cast<const uint2 *>(&As[0][kk][ty * TM + 2]);
+                const uint2 a1l = *reinterpret_cast<const uint2 *>(&As[1][kk][ty * TM]);
+                const uint2 a1h = *reinterpret_cast<const uint2 *>(&As[1][kk][ty * TM + 2]);
                 const uint2 b0 = *reinterpret_cast<const uint2 *>(&Bs[0][kk][tx * TN]);
                 const uint2 b1 = *reinterpret_cast<const uint2 *>(&Bs[1][kk][tx * TN]);
-                const uint32_t av[2][TM] = {{a0.x, a0.y, a0.z, a0.w}, {a1.x, a1.y, a1.z, a1.w}};
+                const uint32_t av[2][TM] = {{a0l.x, a0l.y, a0h.x, a0h.y}, {a1l.x, a1l.y, a1h.x, a1h.y}};
                 const uint32_t bv[2][TN] = {{b0.x, b0.y}, {b1.x, b1.y}};
 #pragma unroll
                 for (int i = 0; i < TM; ++i)

@@ -207,3 +207,34 @@ def test_ccmm_tcgen05_variant_bit_exact(tiny, gpu_run):
         assert np.array_equal(s.residues(), tiny["C"])
     finally:
         C.icm_ctx_set_variant(eng.ctx, 0)
+
+
+def test_ccmm_tcgen05_two_column_rounds_ragged_rows(tiny):
+    """tcgen05 variant on 20 eyes (620 columns: two column rounds, the second with a ragged
+    column tile) against 300 codes (a ragged last row tile): identical to the mma.sync variant
+    everywhere and to the oracle's product on sampled rows, including the ragged tail."""
+    from paper_2601_17561_gb300 import icm as C
+    P = tiny["P"]
+    W = synth.make_workload(n_eyes=20, n_db=300, seed=11, planted_frac=0.05)
+    eng = E.Engine(**E.TINY).keygen()
+    db = eng.encrypt_db(W.db_codes, W.db_masks)
+    ct = eng.encrypt_query(W.q_codes, W.q_masks, W.eye_ids)
+    res = {}
+    try:
+        for v in (256, 1):
+            C.icm_ctx_set_variant(eng.ctx, v)
+            q = eng.prepare(ct, 20, "f16_crt")
+            s = eng.match(db, q)
+            torch.cuda.synchronize()
+            res[v] = s.residues()
+    finally:
+        C.icm_ctx_set_variant(eng.ctx, 0)
+    C.icm_device_status(True)
+    assert np.array_equal(res[1], res[256])
+    ids = O.db_layout(300, P.ndb, P.rho)
+    A = O.db_rows(P, W.db_codes, W.db_masks, ids)
+    Bq = O.query_extend(P, O.query_encrypt(P, W.q_codes, W.q_masks, W.eye_ids))
+    M = A.shape[1]
+    rows = np.unique(np.concatenate([np.arange(0, 8), np.arange(M // 2, M // 2 + 8), np.arange(M - 24, M)]))
+    ref = O.ppmm(P.q, np.ascontiguousarray(A[:, rows, :]), Bq)
+    assert np.array_equal(res[1][:, :, rows], ref)
