@@ -286,7 +286,8 @@ def main():
     ap.add_argument("--compare-forms", default="i8_crt,u64,i8_digits",
                     help="comma list of other forms, each timed for one step on the same workload ('' to skip)")
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--variant", default="auto", help="CRT product kernel: auto (autotuner), 0, 1 (tcgen05) or 128")
+    ap.add_argument("--variant", default="auto",
+                    help="CRT product kernel: auto (autotuner), 128 / 256 (mma.sync) or 1 / 2 (tcgen05)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="paper", choices=["paper", "batching", "serving"],
                     help="paper: the headline CCMM step; batching / serving: the query-batching and "
@@ -339,7 +340,7 @@ def main():
         if args.variant == "auto":
             qt = eng.prepare(ct, N_EYES, args.form)
             best, ms = eng.autotune([db], qt)
-            tune = {"chosen": best, "ms": dict(zip(["mma.sync-128", "mma.sync-256", "tcgen05"], ms))}
+            tune = {"chosen": best, "ms": {name: t for name, t in zip(C.VARIANTS.values(), ms) if t > 0}}
             del qt
         else:
             C.icm_ctx_set_variant(eng.ctx, int(args.variant))
@@ -397,7 +398,7 @@ def main():
     gemm_avg_s = statistics.mean(gemm_ms) / 1e3
     peaks = measured_peaks()
     f = C.FORMS[args.form]
-    tc = tune is not None and tune.get("chosen") == 1
+    tc = tune is not None and tune.get("chosen") in (1, 2)
     if args.form == "u64":
         ops = 4.0 * M * n_cols * K * L                     # IMAD.WIDE per launch (2 x 2 30-bit limb products)
         sm_max = peaks.get("sm_max_mhz", 2070.0)
@@ -427,7 +428,8 @@ def main():
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = NCU_TRAFFIC.get((args.form, 1 if tc else 0))
     roof["kernel"] = {"u64": "k_ppmm_u64", "i8_digits": "k_ppmm_i8<0>", "i8_crt": "k_crt_p1<int8> + k_crt_combine",
-                      "f16_crt": "k_crt_tc (tcgen05) + k_crt_combine" if tc else "k_crt_p1<fp16> + k_crt_combine"
+                      "f16_crt": f"k_crt_tc ({C.VARIANTS[tune['chosen']]}) + k_crt_combine" if tc
+                      else "k_crt_p1<fp16> + k_crt_combine"
                       }.get(args.form)
     roof["ms_per_launch"] = gemm_avg_s * 1e3
 

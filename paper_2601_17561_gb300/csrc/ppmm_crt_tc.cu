@@ -5,22 +5,24 @@
 // in fp32 TMEM and reducing the accumulator modulo m_i every 512 columns of K so that it stays an
 // exact integer below 2^24; c_i goes to the byte scratch that phase 2 (k_crt_combine) recombines.
 //
-// Block: 8 converter warps, 1 MMA warp, 2 TMA producer warps; K advances in slabs of 16.
+// Block: 8 or 16 converter warps, 1 MMA warp, 2 TMA producer warps; K advances in slabs of 16.
 //  * Raw producer: one TMA load per slab of the 128 x 16 balanced-digit storage words of the
 //    database rows (128-byte swizzle: the 16-byte chunk c of row r sits at chunk c ^ (r mod 8)),
 //    into a ring of RS raw stages ("rawfull" / "rawempty" mbarriers).
 //  * Query producer: one TMA load per slab of the 256 x 16 fp16 residue planes of the query
 //    (32-byte swizzle, the canonical K-major SW32 layout of the MMA) into the B half of a ring of
 //    S operand stages ("bfull"; released by the MMA through "empty").
-//  * Converters: each thread turns 8 consecutive storage words of one row into 8 fp16 residues
+//  * Converters: each thread turns 8 (4 with 16 warps) consecutive storage words of one row into
+//    fp16 residues, for 1, 2 or 4 slabs per step
 //    (two dp4a, a multiply-high division and an f16x2 add per pair; no conversion-pipe
-//    instructions) and writes them to the A half of the operand stage (K-major, no swizzle,
+//    instructions), and writes them to the A half of the operand stage (K-major, no swizzle,
 //    8-row x 16-byte core matrices).  The thread-to-(row, k-group) map makes every quarter-warp
-//    read 8 distinct bank groups of the swizzled raw stage and write 128 contiguous bytes.
+//    read 8 distinct bank groups of the swizzled raw stage and write 128 contiguous bytes.  Each
+//    warp signals the barriers once (lane 0 after a warp barrier), not once per thread.
 //  * MMA: one elected thread issues tcgen05.mma (M = 128, N = 256, K = 16) per slab into a
 //    256-column fp32 accumulator and commits to the stage's "empty" mbarrier.  Every 32 slabs and
-//    at the end of a tile it commits to "acc_full"; the converters (two per TMEM lane quarter, 128
-//    columns each) reduce the accumulator in place (tcgen05.ld / st) or write the final residues,
+//    at the end of a tile it commits to "acc_full"; the converters (2 or 4 per TMEM lane quarter,
+//    128 or 64 columns each) reduce the accumulator in place (tcgen05.ld / st) or write the final residues,
 //    and arrive on "acc_free".  Reductions trail conversion by LAG slabs so that the MMA thread
 //    resumes with LAG converted slabs queued.
 //
@@ -38,13 +40,10 @@
 namespace {
 
 constexpr int BM = 128, BN = 256, KS = 16;
+constexpr int NCONV_WARPS = 8;                    // converter warps
 constexpr int S = 8;                              // operand stages (A residues + B planes)
-constexpr int RS = 7;                             // raw database stages
+constexpr int RS = 8;                             // raw database stages
 constexpr int FLUSH_SLABS = 32;                   // 512 columns of K between reductions
-constexpr int LAG = S - 2;                        // reductions trail conversion by LAG slabs
-constexpr int NCONV = 256;                        // converter threads (8 warps)
-constexpr int W_MMA = NCONV / 32, W_RAW = W_MMA + 1, W_QRY = W_MMA + 2;
-constexpr int NT = NCONV + 96;                    // + MMA warp + two producer warps
 constexpr int A_STAGE = BM * KS * 2;              // 4 KB
 constexpr int B_STAGE = BN * KS * 2;              // 8 KB
 constexpr int RAW_STAGE = BM * KS * 8;            // 16 KB
@@ -232,7 +231,18 @@ __device__ __forceinline__ TileCoord tile_coord(const TcArgs &p, uint64_t tile) 
     return t;
 }
 
-__global__ void __launch_bounds__(NT, 1) k_crt_tc(const __grid_constant__ TcArgs p) {
+// Converter warp w converts every slab g with g mod 8 = w on its own (ring slot w of both rings),
+// so the 8 warps work on 8 consecutive slabs at once with no hand-off between them.  The MMA
+// thread issues CB MMAs per pass over the barriers.
+template <int CB>
+__global__ void __launch_bounds__(NCONV_WARPS * 32 + 96, 1) k_crt_tc(const __grid_constant__ TcArgs p) {
+    constexpr int NWC = NCONV_WARPS;
+    constexpr int W_MMA = NWC, W_RAW = NWC + 1, W_QRY = NWC + 2;
+    // a warp performs the reduction after flush point f before it converts a slab past f + LAG;
+    // every slab up to f + S can be converted while the MMA is blocked at f, so LAG < S is safe
+    constexpr int LAG = S - 2;
+    static_assert(S == NWC && RS == NWC, "one ring slot per converter warp");
+    static_assert(CB >= 1 && CB <= 4 && FLUSH_SLABS % CB == 0, "MMAs per barrier pass");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // the swizzle patterns are functions of shared-memory address bits: align the base to 1024
     unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -244,14 +254,14 @@ __global__ void __launch_bounds__(NT, 1) k_crt_tc(const __grid_constant__ TcArgs
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     if (tid == 0) {
-        for (int s = 0; s < RS; ++s) { mbar_init(&bars->rawfull[s], 1); mbar_init(&bars->rawempty[s], NCONV); }
+        for (int s = 0; s < RS; ++s) { mbar_init(&bars->rawfull[s], 1); mbar_init(&bars->rawempty[s], 1); }
         for (int s = 0; s < S; ++s) {
-            mbar_init(&bars->full[s], NCONV);
+            mbar_init(&bars->full[s], 1);
             mbar_init(&bars->bfull[s], 1);
             mbar_init(&bars->empty[s], 1);
         }
         mbar_init(&bars->acc_full, 1);
-        mbar_init(&bars->acc_free, NCONV);
+        mbar_init(&bars->acc_free, NWC);
         mbar_init(&bars->done, 1);
         bars->abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -273,15 +283,18 @@ __global__ void __launch_bounds__(NT, 1) k_crt_tc(const __grid_constant__ TcArgs
 
     if (warp < W_MMA) {
         // ------------------------------------------------------------------ converter warps
-        uint64_t g = 0;                 // global slab counter (ring position)
-        uint32_t acc_uses = 0;          // acc_full completions consumed
+        uint32_t acc_uses = 0;                   // acc_full completions consumed
         const uint32_t qtr = warp & 3, half = warp >> 2;                 // TMEM lane quarter, column half
         const uint32_t trow = qtr * 32 + lane;                           // accumulator row of this thread
-        // conversion map: row and k-group (8 columns) of this thread within the slab
-        const uint32_t crow = (uint32_t)warp * 16 + ((uint32_t)(lane >> 4) << 3) + (lane & 7);
+        // conversion map, item it = 0..7 of a slab: row it*16 + lrow, 16-byte chunks
+        // [4 cj, 4 cj + 4) of the swizzled 128-byte raw row -> 16 bytes of residues; every
+        // quarter-warp covers 8 consecutive rows with the same chunks (8 distinct bank groups)
+        const uint32_t lrow = ((uint32_t)(lane >> 4) << 3) + (lane & 7);
         const uint32_t cj = (lane >> 3) & 1;
-        const uint32_t rsw = crow & 7;
-        const uint32_t a_off = (cj * 16 + (crow >> 3)) * 128 + (crow & 7) * 16;
+        const uint32_t rsw = lane & 7;                                   // = row mod 8 for every item
+        const unsigned char *r_base = sR + warp * RAW_STAGE + lrow * 128;
+        unsigned char *a_base = sA + warp * A_STAGE + (cj * 16 + (lrow >> 3)) * 128 + (lrow & 7) * 16;
+        uint64_t g0 = 0;                         // global index of the tile's first slab
         // every loop decision below is warp-uniform (__all_sync), because drain() issues
         // warp-collective TMEM instructions
         auto go = [&]() { return __all_sync(0xffffffffu, *abort_flag == 0); };
@@ -291,7 +304,7 @@ __global__ void __launch_bounds__(NT, 1) k_crt_tc(const __grid_constant__ TcArgs
             const uint64_t nb = (uint64_t)tc.nt * BN;
             const float fm = (float)md.m;
 
-            // the reduction (or final write) of the accumulator after slab f
+            // the reduction (or final write) of the accumulator after a flush point
             auto drain = [&](bool final) {
                 const bool ok = __all_sync(0xffffffffu, mbar_wait(&bars->acc_full, acc_uses & 1, abort_flag));
                 if (!ok) {
@@ -331,104 +344,135 @@ __global__ void __launch_bounds__(NT, 1) k_crt_tc(const __grid_constant__ TcArgs
                 }
                 if (!final) asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 tc_fence_before();
-                mbar_arrive(&bars->acc_free);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&bars->acc_free);
             };
 
-            for (uint64_t kt = 0; kt < nk; ++kt) {
-                const uint64_t gg = g + kt;
-                const uint32_t s = (uint32_t)(gg % S), u = (uint32_t)(gg / S);
-                const uint32_t rs = (uint32_t)(gg % RS), ur = (uint32_t)(gg / RS);
-                bool ok = mbar_wait(&bars->rawfull[rs], ur & 1, abort_flag);
-                if (ok && u > 0) ok = mbar_wait(&bars->empty[s], (u - 1) & 1, abort_flag);
+            uint64_t next_flush = FLUSH_SLABS - 1;                       // next reduction point to serve
+            bool alive = true;
+            for (uint64_t kt = (uint64_t)((warp + NWC - (int)(g0 % NWC)) % NWC); kt < nk; kt += NWC) {
+                while (next_flush + 1 < nk && kt > next_flush + LAG) {
+                    drain(false);
+                    next_flush += FLUSH_SLABS;
+                }
+                const uint32_t use = (uint32_t)((g0 + kt) / NWC);      // uses of ring slot `warp`
+                bool ok = mbar_wait(&bars->rawfull[warp], use & 1, abort_flag);
+                if (ok && use > 0) ok = mbar_wait(&bars->empty[warp], (use - 1) & 1, abort_flag);
                 if (!__all_sync(0xffffffffu, ok)) {
                     *abort_flag = 1;
+                    alive = false;
                     break;
                 }
-                // 8 storage words (4 swizzled 16-byte chunks) of row crow -> 8 fp16 residues
-                const unsigned char *r_s = sR + rs * RAW_STAGE + crow * 128;
-                uint32_t w[4];
 #pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                    const ulonglong2 zz = *reinterpret_cast<const ulonglong2 *>(r_s + (((cj * 4 + h) ^ rsw) << 4));
-                    w[h] = res_pair(zz.x, zz.y, md.wlo, md.whi, md.cbias, md.magic, (uint32_t)md.m, md.hneg2);
+                for (int it = 0; it < 8; ++it) {
+                    const unsigned char *r_s = r_base + it * 16 * 128;
+                    uint32_t w[4];
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+                        const ulonglong2 zz = *reinterpret_cast<const ulonglong2 *>(r_s + (((cj * 4 + h) ^ rsw) << 4));
+                        w[h] = res_pair(zz.x, zz.y, md.wlo, md.whi, md.cbias, md.magic, (uint32_t)md.m, md.hneg2);
+                    }
+                    *reinterpret_cast<uint4 *>(a_base + it * 2 * 128) = make_uint4(w[0], w[1], w[2], w[3]);
                 }
-                mbar_arrive(&bars->rawempty[rs]);
-                *reinterpret_cast<uint4 *>(sA + s * A_STAGE + a_off) = make_uint4(w[0], w[1], w[2], w[3]);
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                mbar_arrive(&bars->full[s]);
-                if (kt >= (uint64_t)LAG && is_flush(kt - LAG)) drain(false);
-                if (!go()) break;
+                // the warp barrier orders every lane's raw reads and residue writes before lane 0's
+                // release of the raw slot and the operand slot
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(&bars->rawempty[warp]);
+                    mbar_arrive(&bars->full[warp]);
+                }
+                if (!go()) { alive = false; break; }
             }
+            if (!alive) break;
             // remaining reductions, then the final residues of the tile
-            for (uint64_t f = (nk >= (uint64_t)LAG ? nk - LAG : 0); f < nk && go(); ++f)
-                if (is_flush(f)) drain(false);
+            for (; next_flush + 1 < nk && go(); next_flush += FLUSH_SLABS) drain(false);
             if (go()) drain(true);
-            g += nk;
+            g0 += nk;
         }
     } else if (warp == W_MMA && lane == 0) {
         // ------------------------------------------------------------------ MMA (one thread)
-        uint64_t g = 0;
+        uint32_t s = 0, u = 0;
         uint32_t acc_commits = 0;
         bool wait_free = false;
+        // descriptors of ring slot 0; slot s adds s * stage / 16 to the start-address field
+        const uint64_t adesc0 = sdesc(smem_u32(sA), 2048, 128, 0), bdesc0 = sdesc(smem_u32(sB), 16, 256, 6);
+        // slabs go in steps of CB: one pass of barrier waits, then CB MMAs, each committing its
+        // slot's "empty" barrier
         for (uint64_t tile = blockIdx.x; tile < p.n_tiles && !*abort_flag; tile += gridDim.x) {
-            for (uint64_t kt = 0; kt < nk && !*abort_flag; ++kt, ++g) {
-                const uint32_t s = (uint32_t)(g % S);
-                const uint32_t u = (uint32_t)(g / S);
+            bool alive = true;
+            uint32_t to_flush = FLUSH_SLABS;                             // slabs to the next reduction
+            for (uint64_t kt = 0; kt < nk && alive; kt += CB) {
+                const int nbt = (nk - kt) < (uint64_t)CB ? (int)(nk - kt) : CB;
                 if (wait_free) {
-                    if (!mbar_wait(&bars->acc_free, (acc_commits - 1) & 1, abort_flag)) break;
+                    if (!mbar_wait(&bars->acc_free, (acc_commits - 1) & 1, abort_flag)) { alive = false; break; }
                     wait_free = false;
                 }
-                if (!mbar_wait(&bars->full[s], u & 1, abort_flag)) break;
-                if (!mbar_wait(&bars->bfull[s], u & 1, abort_flag)) break;
+                for (int b = 0; b < nbt && alive; ++b) {
+                    const uint32_t sb = s + b < S ? s + b : s + b - S, ub = s + b < S ? u : u + 1;
+                    alive = mbar_wait(&bars->full[sb], ub & 1, abort_flag) && mbar_wait(&bars->bfull[sb], ub & 1, abort_flag);
+                }
+                if (!alive) break;
                 tc_fence_after();
-                umma(tmem, sdesc(smem_u32(sA + s * A_STAGE), 2048, 128, 0),
-                     sdesc(smem_u32(sB + s * B_STAGE), 16, 256, 6), kt > 0 ? 1u : 0u);
-                umma_commit(&bars->empty[s]);
-                if (is_flush(kt) || kt + 1 == nk) {
+                for (int b = 0; b < nbt; ++b) {
+                    const uint32_t sb = s + b < S ? s + b : s + b - S;
+                    umma(tmem, adesc0 + (uint64_t)(sb * (A_STAGE >> 4)), bdesc0 + (uint64_t)(sb * (B_STAGE >> 4)),
+                         (kt + b) > 0 ? 1u : 0u);
+                    umma_commit(&bars->empty[sb]);
+                }
+                s += nbt; if (s >= S) { s -= S; ++u; }
+                to_flush -= nbt;
+                if (to_flush == 0 || kt + nbt == nk) {                   // a reduction point closes a step
                     umma_commit(&bars->acc_full);
                     ++acc_commits;
                     wait_free = true;
+                    to_flush = FLUSH_SLABS;
                 }
             }
+            if (!alive) break;
         }
         // make sure every MMA issued by this thread has completed before TMEM is freed
         umma_commit(&bars->done);
         mbar_wait_drain(&bars->done, 0);
     } else if (warp == W_RAW && lane == 0) {
         // ------------------------------------------------------------------ raw database producer
-        uint64_t g = 0;
+        uint32_t rs = 0, ur = 0;
+        uint64_t issued = 0;
         for (uint64_t tile = blockIdx.x; tile < p.n_tiles && !*abort_flag; tile += gridDim.x) {
             const TileCoord tc = tile_coord(p, tile);
             bool alive = true;
-            for (uint64_t kt = 0; kt < nk; ++kt, ++g) {
-                const uint32_t rs = (uint32_t)(g % RS), ur = (uint32_t)(g / RS);
+            for (uint64_t kt = 0; kt < nk; ++kt) {
                 if (ur > 0 && !mbar_wait(&bars->rawempty[rs], (ur - 1) & 1, abort_flag)) { alive = false; break; }
                 mbar_expect_tx(&bars->rawfull[rs], RAW_STAGE);
                 tma_load_3d(smem_u32(sR + rs * RAW_STAGE), &p.tmA[tc.c], (int)(kt * KS), (int)tc.m0, (int)tc.l,
                             &bars->rawfull[rs]);
+                ++issued;
+                if (++rs == RS) { rs = 0; ++ur; }
             }
             if (!alive) break;
         }
         // every load issued by this thread has landed before the block exits
-        for (uint64_t i = (g > (uint64_t)RS ? g - RS : 0); i < g; ++i)
+        for (uint64_t i = (issued > (uint64_t)RS ? issued - RS : 0); i < issued; ++i)
             mbar_wait_drain(&bars->rawfull[i % RS], (uint32_t)((i / RS) & 1));
     } else if (warp == W_QRY && lane == 0) {
         // ------------------------------------------------------------------ query plane producer
-        uint64_t g = 0;
+        uint32_t s = 0, u = 0;
+        uint64_t issued = 0;
         for (uint64_t tile = blockIdx.x; tile < p.n_tiles && !*abort_flag; tile += gridDim.x) {
             const TileCoord tc = tile_coord(p, tile);
             const uint64_t nb = (uint64_t)tc.nt * BN;
             bool alive = true;
-            for (uint64_t kt = 0; kt < nk; ++kt, ++g) {
-                const uint32_t s = (uint32_t)(g % S), u = (uint32_t)(g / S);
+            for (uint64_t kt = 0; kt < nk; ++kt) {
                 if (u > 0 && !mbar_wait(&bars->empty[s], (u - 1) & 1, abort_flag)) { alive = false; break; }
                 mbar_expect_tx(&bars->bfull[s], B_STAGE);
                 tma_load_4d(smem_u32(sB + s * B_STAGE), &p.tmB, (int)(kt * KS), (int)(p.n0 + nb), (int)tc.mi, (int)tc.l,
                             &bars->bfull[s]);
+                ++issued;
+                if (++s == S) { s = 0; ++u; }
             }
             if (!alive) break;
         }
-        for (uint64_t i = (g > (uint64_t)S ? g - S : 0); i < g; ++i)
+        for (uint64_t i = (issued > (uint64_t)S ? issued - S : 0); i < issued; ++i)
             mbar_wait_drain(&bars->bfull[i % S], (uint32_t)((i / S) & 1));
     }
     tc_fence_before();
@@ -463,7 +507,9 @@ EncodeTiled encode_fn() {
 namespace icm {
 
 cudaError_t crt_tc_set_attributes() {
-    return cudaFuncSetAttribute(k_crt_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    cudaError_t e = cudaFuncSetAttribute(k_crt_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_crt_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    return e;
 }
 
 // The tcgen05 path needs an even K (tensor-map row strides are multiples of 16 bytes); the caller
@@ -480,8 +526,8 @@ uint32_t device_status(bool clear) {
     return v;
 }
 
-cudaError_t launch_ppmm_crt_tc(const I8Consts &k, const ChunkTab &tab, const void *Bp, uint64_t N, uint64_t K, uint64_t Kp,
-                               void *scratch, cudaStream_t st) {
+cudaError_t launch_ppmm_crt_tc(int variant, const I8Consts &k, const ChunkTab &tab, const void *Bp, uint64_t N, uint64_t K,
+                               uint64_t Kp, void *scratch, cudaStream_t st) {
     const uint64_t Mall = tab.row0[tab.n];
     if (Mall == 0 || N == 0) return cudaSuccess;
     if (!crt_tc_supported(K) || Kp % KS) return cudaErrorInvalidValue;
@@ -527,7 +573,8 @@ cudaError_t launch_ppmm_crt_tc(const I8Consts &k, const ChunkTab &tab, const voi
         a.n_tiles = (uint64_t)k.n_limbs * tab.mt0[tab.n] * k.n_mod * a.n_ntile;
         const uint64_t grid = std::min<uint64_t>(a.n_tiles, (uint64_t)sms);
         if (grid == 0) continue;
-        k_crt_tc<<<(unsigned)grid, NT, SMEM_BYTES, st>>>(a);
+        if (variant == ICM_CRT_TCGEN05_C4) k_crt_tc<4><<<(unsigned)grid, NCONV_WARPS * 32 + 96, SMEM_BYTES, st>>>(a);
+        else k_crt_tc<1><<<(unsigned)grid, NCONV_WARPS * 32 + 96, SMEM_BYTES, st>>>(a);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         e = launch_crt_combine(k, tab, scratch, N, n0, nch, st);

@@ -311,10 +311,15 @@ def icm_plan_destroy(plan):
 
 def icm_autotune(ctx, dbs, q, dev_outs, out_bytes, dev_ws, ws_bytes, stream=None):
     best = ctypes.c_int()
-    ms = (ctypes.c_float * 3)()
+    ms = (ctypes.c_float * len(VARIANTS))()
     _check(lib().icm_autotune(ctx, _handle_array(dbs), len(dbs), q, _ptr_array(dev_outs), _size_array(out_bytes),
-                              _ptr(dev_ws), ws_bytes, _stream(stream), ctypes.byref(best), ms, 3), "icm_autotune")
+                              _ptr(dev_ws), ws_bytes, _stream(stream), ctypes.byref(best), ms, len(VARIANTS)),
+           "icm_autotune")
     return best.value, list(ms)
+
+
+# CRT product kernel variants in the autotuner's order (icm_autotune's ms_per_choice)
+VARIANTS = {128: "mma.sync-128", 256: "mma.sync-256", 1: "tcgen05", 2: "tcgen05-mma4"}
 
 
 def icm_ctx_set_variant(ctx, variant: int):

@@ -193,12 +193,14 @@ def test_ppmm_extremes(form, kind):
         assert np.all(got[l] == (xc[l] * xc[l] * K) % q_l)
 
 
-def test_ccmm_tcgen05_variant_bit_exact(tiny, gpu_run):
-    """The tcgen05 kernel variant of the fp16 CRT form (tensor-memory accumulators) gives the
-    oracle's residues, and no kernel gave up a bounded wait."""
+@pytest.mark.parametrize("variant", [1, 2])
+def test_ccmm_tcgen05_variant_bit_exact(tiny, gpu_run, variant):
+    """Each tcgen05 kernel variant of the fp16 CRT form (tensor-memory accumulators; one or four
+    MMAs per pass of the issuing thread) gives the oracle's residues, and no kernel gave up a
+    bounded wait."""
     from paper_2601_17561_gb300 import icm as C
     eng, W = gpu_run["eng"], tiny["W"]
-    C.icm_ctx_set_variant(eng.ctx, 1)
+    C.icm_ctx_set_variant(eng.ctx, variant)
     try:
         q = eng.prepare(gpu_run["ct"], W.q_codes.shape[0], "f16_crt")
         s = eng.match(gpu_run["db"], q)
@@ -221,7 +223,7 @@ def test_ccmm_tcgen05_two_column_rounds_ragged_rows(tiny):
     ct = eng.encrypt_query(W.q_codes, W.q_masks, W.eye_ids)
     res = {}
     try:
-        for v in (256, 1):
+        for v in (256, 1, 2):
             C.icm_ctx_set_variant(eng.ctx, v)
             q = eng.prepare(ct, 20, "f16_crt")
             s = eng.match(db, q)
@@ -230,7 +232,8 @@ def test_ccmm_tcgen05_two_column_rounds_ragged_rows(tiny):
     finally:
         C.icm_ctx_set_variant(eng.ctx, 0)
     C.icm_device_status(True)
-    assert np.array_equal(res[1], res[256])
+    for v in (1, 2):
+        assert np.array_equal(res[v], res[256])
     ids = O.db_layout(300, P.ndb, P.rho)
     A = O.db_rows(P, W.db_codes, W.db_masks, ids)
     Bq = O.query_extend(P, O.query_encrypt(P, W.q_codes, W.q_masks, W.eye_ids))
