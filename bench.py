@@ -287,7 +287,7 @@ def main():
                     help="comma list of other forms, each timed for one step on the same workload ('' to skip)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--variant", default="auto",
-                    help="CRT product kernel: auto (autotuner), 128 / 256 (mma.sync) or 1 / 2 (tcgen05)")
+                    help="CRT product kernel: auto (autotuner), 128 / 256 (mma.sync) or 1 (tcgen05)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="paper", choices=["paper", "batching", "serving"],
                     help="paper: the headline CCMM step; batching / serving: the query-batching and "
@@ -398,7 +398,7 @@ def main():
     gemm_avg_s = statistics.mean(gemm_ms) / 1e3
     peaks = measured_peaks()
     f = C.FORMS[args.form]
-    tc = tune is not None and tune.get("chosen") in (1, 2)
+    tc = tune is not None and tune.get("chosen") == 1
     if args.form == "u64":
         ops = 4.0 * M * n_cols * K * L                     # IMAD.WIDE per launch (2 x 2 30-bit limb products)
         sm_max = peaks.get("sm_max_mhz", 2070.0)

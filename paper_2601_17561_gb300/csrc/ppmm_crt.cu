@@ -379,7 +379,7 @@ cudaError_t launch_ppmm_crt_grouped(bool f16, int bn, const I8Consts &k, const C
     const uint64_t Mall = tab.row0[tab.n];
     if (Mall == 0 || N == 0) return cudaSuccess;
     if (f16 && crt_tc_variant(bn) && tab.a_digits && crt_tc_supported(K))
-        return launch_ppmm_crt_tc(bn, k, tab, Bp, N, K, Kp, scratch, st);
+        return launch_ppmm_crt_tc(k, tab, Bp, N, K, Kp, scratch, st);
     if (bn != 128) bn = 256;
     for (uint64_t n0 = 0; n0 < N; n0 += NCHUNK) {
         const uint64_t nch = std::min<uint64_t>(NCHUNK, N - n0);

@@ -1,30 +1,32 @@
 // Phase 1 of the fp16 small-modulus CRT product on the tcgen05 tensor cores (Blackwell 5th-gen
 // MMA with accumulators in tensor memory).  Same arithmetic as k_crt_p1<fp16> (ppmm_crt.cu):
-// for one (limb, database chunk, 128-row tile, modulus m_i, 256-column tile) it computes
-// c_i = (sum_k a[k] b[k]) mod m_i over residues held exactly in fp16 (|r| <= 128), accumulating
-// in fp32 TMEM and reducing the accumulator modulo m_i every 512 columns of K so that it stays an
-// exact integer below 2^24; c_i goes to the byte scratch that phase 2 (k_crt_combine) recombines.
+// for one (limb, database chunk, 128-row tile, pair of moduli m_i, m_i+1, 256-column tile) it
+// computes c_i = (sum_k a[k] b[k]) mod m_i over residues held exactly in fp16 (|r| <= 128),
+// accumulating in fp32 TMEM (one 256-column accumulator per modulus, all 512 columns) and
+// reducing the accumulators modulo m_i every 512 columns of K so that they stay exact integers
+// below 2^24; c_i goes to the byte scratch that phase 2 (k_crt_combine) recombines.
 //
-// Block: 8 or 16 converter warps, 1 MMA warp, 2 TMA producer warps; K advances in slabs of 16.
+// Pairing the moduli halves the shared-memory traffic and conversion overhead per modulus: the
+// raw database slab is loaded and read once for two MMAs.
+//
+// Block: 8 converter warps, 1 MMA warp, 2 TMA producer warps; K advances in slabs of 16.
 //  * Raw producer: one TMA load per slab of the 128 x 16 balanced-digit storage words of the
 //    database rows (128-byte swizzle: the 16-byte chunk c of row r sits at chunk c ^ (r mod 8)),
-//    into a ring of RS raw stages ("rawfull" / "rawempty" mbarriers).
-//  * Query producer: one TMA load per slab of the 256 x 16 fp16 residue planes of the query
-//    (32-byte swizzle, the canonical K-major SW32 layout of the MMA) into the B half of a ring of
-//    S operand stages ("bfull"; released by the MMA through "empty").
-//  * Converters: each thread turns 8 (4 with 16 warps) consecutive storage words of one row into
-//    fp16 residues, for 1, 2 or 4 slabs per step
-//    (two dp4a, a multiply-high division and an f16x2 add per pair; no conversion-pipe
-//    instructions), and writes them to the A half of the operand stage (K-major, no swizzle,
-//    8-row x 16-byte core matrices).  The thread-to-(row, k-group) map makes every quarter-warp
-//    read 8 distinct bank groups of the swizzled raw stage and write 128 contiguous bytes.  Each
-//    warp signals the barriers once (lane 0 after a warp barrier), not once per thread.
-//  * MMA: one elected thread issues tcgen05.mma (M = 128, N = 256, K = 16) per slab into a
-//    256-column fp32 accumulator and commits to the stage's "empty" mbarrier.  Every 32 slabs and
-//    at the end of a tile it commits to "acc_full"; the converters (2 or 4 per TMEM lane quarter,
-//    128 or 64 columns each) reduce the accumulator in place (tcgen05.ld / st) or write the final residues,
-//    and arrive on "acc_free".  Reductions trail conversion by LAG slabs so that the MMA thread
-//    resumes with LAG converted slabs queued.
+//    into a ring of RS raw slots ("rawfull" / "rawempty" mbarriers).
+//  * Query producer: per slab, one TMA load per modulus of the 256 x 16 fp16 residue planes of
+//    the query (32-byte swizzle, the canonical K-major SW32 layout of the MMA) into the B half of a
+//    ring of S operand slots ("bfull"; released by the MMA through "empty").
+//  * Converters: warps w and w + 4 own operand slot w and raw slots w and w + 4, and convert every
+//    slab g with g mod 4 = w, 64 rows each: 8 consecutive storage words of a row become 8 fp16
+//    residues per modulus (two dp4a, a multiply-high division and an f16x2 add per pair; no
+//    conversion-pipe instructions), written to the A half of the slot (K-major, no swizzle, 8-row
+//    x 16-byte core matrices).  Every quarter-warp reads 8 distinct bank groups of the swizzled
+//    raw slot and writes 128 contiguous bytes.
+//  * MMA: one elected thread issues one tcgen05.mma (M = 128, N = 256, K = 16) per modulus and
+//    slab and commits to the slot's "empty" mbarrier.  Every 32 slabs and at the end of a tile it
+//    commits to "acc_full"; the converters (warps w mod 4 = q serve TMEM lane quarter q, warps 0-3
+//    the first accumulator and 4-7 the second) reduce the accumulators in place (tcgen05.ld / st)
+//    or write the final residues, and arrive on "acc_free".
 //
 // Every wait is bounded by %globaltimer (2 s); on expiry the block records ICM_DEV_TIMEOUT in the
 // device status word, stops issuing work, waits (bounded) for its own MMAs and TMA loads, and
@@ -40,23 +42,24 @@
 namespace {
 
 constexpr int BM = 128, BN = 256, KS = 16;
-constexpr int NCONV_WARPS = 8;                    // converter warps
-constexpr int S = 8;                              // operand stages (A residues + B planes)
-constexpr int RS = 8;                             // raw database stages
+constexpr int NWC = 8;                            // converter warps (two per operand slot)
+constexpr int S = 4;                              // operand slots (A residues + B planes, 2 moduli)
+constexpr int RS = 8;                             // raw database slots
 constexpr int FLUSH_SLABS = 32;                   // 512 columns of K between reductions
-constexpr int A_STAGE = BM * KS * 2;              // 4 KB
-constexpr int B_STAGE = BN * KS * 2;              // 8 KB
+constexpr int A_STAGE = BM * KS * 2;              // 4 KB per modulus
+constexpr int B_STAGE = BN * KS * 2;              // 8 KB per modulus
 constexpr int RAW_STAGE = BM * KS * 8;            // 16 KB
-constexpr uint32_t TMEM_COLS = 256;
+constexpr uint32_t TMEM_COLS = 512;               // two 256-column fp32 accumulators
 constexpr uint64_t WAIT_NS = 2000000000ull;       // bound of every wait
-// Shared memory: raw stages first (1024-byte aligned for the 128-byte swizzle), then B and A
-// stages, then the mbarriers.
+// Shared memory: raw slots first (1024-byte aligned for the 128-byte swizzle), then the B and A
+// halves of the operand slots (modulus 0 then modulus 1), then the mbarriers.
 constexpr int OFF_B = RS * RAW_STAGE;
-constexpr int OFF_A = OFF_B + S * B_STAGE;
-constexpr int SMEM_RING = OFF_A + S * A_STAGE;
+constexpr int OFF_A = OFF_B + S * 2 * B_STAGE;
+constexpr int SMEM_RING = OFF_A + S * 2 * A_STAGE;
 constexpr int SMEM_BYTES = SMEM_RING + 2048;      // + barriers + slack to align the base to 1024
 static_assert(SMEM_BYTES <= 227 * 1024, "shared memory budget");
 static_assert(OFF_B % 1024 == 0 && OFF_A % 1024 == 0, "stage alignment");
+static_assert(NWC == 2 * S && RS == 2 * S, "slot ownership");
 constexpr uint64_t NCHUNK = 512;
 
 struct TcMod {
@@ -71,7 +74,7 @@ struct TcArgs {
     icm::ChunkTab tab;
     uint8_t *R;                       // [L][r][nch][sum M_c]
     uint64_t N, K, n0, nch;
-    uint32_t n_ntile, n_mod;
+    uint32_t n_ntile, n_mod, n_pair;  // moduli 2 j and 2 j + 1 form pair j (the last may be single)
     uint64_t n_tiles;
     TcMod md[ICM_MAX_MODULI];
 };
@@ -212,14 +215,16 @@ struct __align__(8) Bars {
 static_assert(sizeof(Bars) <= 1024, "barrier block");
 
 struct TileCoord {
-    uint32_t l, c, mi, nt;
+    uint32_t l, c, mi, nt;            // mi: first modulus of the pair
+    bool two;                         // the pair holds a second modulus mi + 1
     uint64_t m0, M;
 };
 __device__ __forceinline__ TileCoord tile_coord(const TcArgs &p, uint64_t tile) {
     TileCoord t;
     uint64_t tt = tile;
     t.nt = (uint32_t)(tt % p.n_ntile); tt /= p.n_ntile;
-    t.mi = (uint32_t)(tt % p.n_mod); tt /= p.n_mod;
+    t.mi = 2 * (uint32_t)(tt % p.n_pair); tt /= p.n_pair;
+    t.two = t.mi + 1 < p.n_mod;
     const uint32_t mt_total = p.tab.mt0[p.tab.n];
     const uint32_t mtg = (uint32_t)(tt % mt_total);
     t.l = (uint32_t)(tt / mt_total);
@@ -231,32 +236,28 @@ __device__ __forceinline__ TileCoord tile_coord(const TcArgs &p, uint64_t tile) 
     return t;
 }
 
-// Converter warp w converts every slab g with g mod 8 = w on its own (ring slot w of both rings),
-// so the 8 warps work on 8 consecutive slabs at once with no hand-off between them.  The MMA
-// thread issues CB MMAs per pass over the barriers.
-template <int CB>
-__global__ void __launch_bounds__(NCONV_WARPS * 32 + 96, 1) k_crt_tc(const __grid_constant__ TcArgs p) {
-    constexpr int NWC = NCONV_WARPS;
+// Converter warps w and w + 4 convert slab g (g mod 4 = w) together, 64 rows each, using operand
+// slot w and raw slot g mod 8; each warp meets its slots' phases in order.  The MMA thread issues
+// one MMA per modulus and slab.
+__global__ void __launch_bounds__(NWC * 32 + 96, 1) k_crt_tc(const __grid_constant__ TcArgs p) {
     constexpr int W_MMA = NWC, W_RAW = NWC + 1, W_QRY = NWC + 2;
     // a warp performs the reduction after flush point f before it converts a slab past f + LAG;
-    // every slab up to f + S can be converted while the MMA is blocked at f, so LAG < S is safe
-    constexpr int LAG = S - 2;
-    static_assert(S == NWC && RS == NWC, "one ring slot per converter warp");
-    static_assert(CB >= 1 && CB <= 4 && FLUSH_SLABS % CB == 0, "MMAs per barrier pass");
+    // a slab y can be converted while the MMA is blocked at f when its slot is free (y - S <= f)
+    constexpr int LAG = S - 1;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // the swizzle patterns are functions of shared-memory address bits: align the base to 1024
     unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     unsigned char *sR = smem;                          // [RS][RAW_STAGE]
-    unsigned char *sB = smem + OFF_B;                  // [S][B_STAGE]
-    unsigned char *sA = smem + OFF_A;                  // [S][A_STAGE]
+    unsigned char *sB = smem + OFF_B;                  // [S][2][B_STAGE]
+    unsigned char *sA = smem + OFF_A;                  // [S][2][A_STAGE]
     Bars *bars = reinterpret_cast<Bars *>(smem + SMEM_RING);
     volatile int *abort_flag = &bars->abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     if (tid == 0) {
-        for (int s = 0; s < RS; ++s) { mbar_init(&bars->rawfull[s], 1); mbar_init(&bars->rawempty[s], 1); }
+        for (int s = 0; s < RS; ++s) { mbar_init(&bars->rawfull[s], 1); mbar_init(&bars->rawempty[s], 2); }
         for (int s = 0; s < S; ++s) {
-            mbar_init(&bars->full[s], 1);
+            mbar_init(&bars->full[s], 2);
             mbar_init(&bars->bfull[s], 1);
             mbar_init(&bars->empty[s], 1);
         }
@@ -279,32 +280,34 @@ __global__ void __launch_bounds__(NCONV_WARPS * 32 + 96, 1) k_crt_tc(const __gri
     const uint64_t K = p.K, N = p.N;
     const uint64_t nk = (K + KS - 1) / KS;
     const uint64_t Mall = p.tab.row0[p.tab.n];
-    auto is_flush = [&](uint64_t f) { return ((f + 1) % FLUSH_SLABS) == 0 && f + 1 < nk; };
 
     if (warp < W_MMA) {
         // ------------------------------------------------------------------ converter warps
         uint32_t acc_uses = 0;                   // acc_full completions consumed
-        const uint32_t qtr = warp & 3, half = warp >> 2;                 // TMEM lane quarter, column half
+        const uint32_t qtr = warp & 3, hacc = warp >> 2;                 // TMEM lane quarter, accumulator
+        const uint32_t slot = warp & 3, half = warp >> 2;                // operand slot, row half
         const uint32_t trow = qtr * 32 + lane;                           // accumulator row of this thread
-        // conversion map, item it = 0..7 of a slab: row it*16 + lrow, 16-byte chunks
-        // [4 cj, 4 cj + 4) of the swizzled 128-byte raw row -> 16 bytes of residues; every
-        // quarter-warp covers 8 consecutive rows with the same chunks (8 distinct bank groups)
-        const uint32_t lrow = ((uint32_t)(lane >> 4) << 3) + (lane & 7);
+        // conversion map, item it = 0..3: row half*64 + it*16 + lrow, 16-byte chunks [4 cj, 4 cj + 4)
+        // of the swizzled 128-byte raw row -> 16 bytes of residues per modulus; every quarter-warp
+        // covers 8 consecutive rows with the same chunks (8 distinct bank groups)
+        const uint32_t lrow = half * 64 + ((uint32_t)(lane >> 4) << 3) + (lane & 7);
         const uint32_t cj = (lane >> 3) & 1;
         const uint32_t rsw = lane & 7;                                   // = row mod 8 for every item
-        const unsigned char *r_base = sR + warp * RAW_STAGE + lrow * 128;
-        unsigned char *a_base = sA + warp * A_STAGE + (cj * 16 + (lrow >> 3)) * 128 + (lrow & 7) * 16;
+        const uint32_t a_off = (cj * 16 + (lrow >> 3)) * 128 + (lrow & 7) * 16;
+        unsigned char *a_slot = sA + slot * 2 * A_STAGE + a_off;
         uint64_t g0 = 0;                         // global index of the tile's first slab
         // every loop decision below is warp-uniform (__all_sync), because drain() issues
         // warp-collective TMEM instructions
         auto go = [&]() { return __all_sync(0xffffffffu, *abort_flag == 0); };
         for (uint64_t tile = blockIdx.x; tile < p.n_tiles && go(); tile += gridDim.x) {
             const TileCoord tc = tile_coord(p, tile);
-            const TcMod md = p.md[tc.mi];
+            const TcMod m0 = p.md[tc.mi], m1 = p.md[tc.two ? tc.mi + 1 : tc.mi];
+            const TcMod md = hacc ? m1 : m0;                             // modulus of this warp's accumulator
+            const bool mine = hacc == 0 || tc.two;                       // this warp's accumulator is in use
             const uint64_t nb = (uint64_t)tc.nt * BN;
             const float fm = (float)md.m;
 
-            // the reduction (or final write) of the accumulator after a flush point
+            // the reduction (or final write) of this warp's part of the accumulators
             auto drain = [&](bool final) {
                 const bool ok = __all_sync(0xffffffffu, mbar_wait(&bars->acc_full, acc_uses & 1, abort_flag));
                 if (!ok) {
@@ -313,36 +316,39 @@ __global__ void __launch_bounds__(NCONV_WARPS * 32 + 96, 1) k_crt_tc(const __gri
                 }
                 ++acc_uses;
                 tc_fence_after();
-                for (int rnd = 0; rnd < 4; ++rnd) {
-                    const uint32_t col0 = half * 128 + rnd * 32;
-                    const uint32_t taddr = tmem + ((qtr * 32) << 16) + col0;
-                    uint32_t v[32];
-                    tmem_ld32(taddr, v);
-                    if (!final) {
-                        // x - m round(x / m): the fma adds 1.5 2^23 to the exact x / m estimate
-                        // and rounds once, which rounds it to an integer (|x / m| < 2^22)
+                if (mine) {
+                    for (int rnd = 0; rnd < 8; ++rnd) {
+                        const uint32_t col0 = rnd * 32;
+                        const uint32_t taddr = tmem + ((qtr * 32) << 16) + hacc * 256 + col0;
+                        uint32_t v[32];
+                        tmem_ld32(taddr, v);
+                        if (!final) {
+                            // x - m round(x / m): the fma adds 1.5 2^23 to the exact x / m
+                            // estimate and rounds once, which rounds it to an integer (|x / m| < 2^22)
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            const float x = __uint_as_float(v[j]);
-                            const float t = __fsub_rn(fmaf(x, md.inv_m, 12582912.0f), 12582912.0f);
-                            v[j] = __float_as_uint(fmaf(-fm, t, x));
-                        }
-                        tmem_st32(taddr, v);
-                    } else {
-                        const uint64_t row = tc.m0 + trow;
-                        uint8_t *Rl = p.R + ((size_t)tc.l * p.n_mod + tc.mi) * p.nch * Mall + p.tab.row0[tc.c];
+                            for (int j = 0; j < 32; ++j) {
+                                const float x = __uint_as_float(v[j]);
+                                const float t = __fsub_rn(fmaf(x, md.inv_m, 12582912.0f), 12582912.0f);
+                                v[j] = __float_as_uint(fmaf(-fm, t, x));
+                            }
+                            tmem_st32(taddr, v);
+                        } else {
+                            const uint64_t row = tc.m0 + trow;
+                            const uint32_t mi = tc.mi + hacc;
+                            uint8_t *Rl = p.R + ((size_t)tc.l * p.n_mod + mi) * p.nch * Mall + p.tab.row0[tc.c];
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            const uint64_t col = nb + col0 + j;
-                            if (row < tc.M && col < p.nch && p.n0 + col < N) {
-                                int val = __float2int_rn(__uint_as_float(v[j])) % md.m;
-                                val = val < 0 ? val + md.m : val;
-                                Rl[col * Mall + row] = (uint8_t)val;
+                            for (int j = 0; j < 32; ++j) {
+                                const uint64_t col = nb + col0 + j;
+                                if (row < tc.M && col < p.nch && p.n0 + col < N) {
+                                    int val = __float2int_rn(__uint_as_float(v[j])) % md.m;
+                                    val = val < 0 ? val + md.m : val;
+                                    Rl[col * Mall + row] = (uint8_t)val;
+                                }
                             }
                         }
                     }
+                    if (!final) asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 }
-                if (!final) asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&bars->acc_free);
@@ -350,37 +356,42 @@ __global__ void __launch_bounds__(NCONV_WARPS * 32 + 96, 1) k_crt_tc(const __gri
 
             uint64_t next_flush = FLUSH_SLABS - 1;                       // next reduction point to serve
             bool alive = true;
-            for (uint64_t kt = (uint64_t)((warp + NWC - (int)(g0 % NWC)) % NWC); kt < nk; kt += NWC) {
+            for (uint64_t kt = (uint64_t)((slot + S - (uint32_t)(g0 % S)) % S); kt < nk; kt += S) {
                 while (next_flush + 1 < nk && kt > next_flush + LAG) {
                     drain(false);
                     next_flush += FLUSH_SLABS;
                 }
-                const uint32_t use = (uint32_t)((g0 + kt) / NWC);      // uses of ring slot `warp`
-                bool ok = mbar_wait(&bars->rawfull[warp], use & 1, abort_flag);
-                if (ok && use > 0) ok = mbar_wait(&bars->empty[warp], (use - 1) & 1, abort_flag);
+                const uint64_t g = g0 + kt;
+                const uint32_t use = (uint32_t)(g / S);                   // uses of operand slot `slot`
+                const uint32_t rslot = (uint32_t)(g % RS), ruse = (uint32_t)(g / RS);
+                bool ok = mbar_wait(&bars->rawfull[rslot], ruse & 1, abort_flag);
+                if (ok && use > 0) ok = mbar_wait(&bars->empty[slot], (use - 1) & 1, abort_flag);
                 if (!__all_sync(0xffffffffu, ok)) {
                     *abort_flag = 1;
                     alive = false;
                     break;
                 }
+                const unsigned char *r_base = sR + rslot * RAW_STAGE + lrow * 128;
 #pragma unroll
-                for (int it = 0; it < 8; ++it) {
+                for (int it = 0; it < 4; ++it) {
                     const unsigned char *r_s = r_base + it * 16 * 128;
-                    uint32_t w[4];
+                    uint32_t w0[4], w1[4];
 #pragma unroll
                     for (int h = 0; h < 4; ++h) {
                         const ulonglong2 zz = *reinterpret_cast<const ulonglong2 *>(r_s + (((cj * 4 + h) ^ rsw) << 4));
-                        w[h] = res_pair(zz.x, zz.y, md.wlo, md.whi, md.cbias, md.magic, (uint32_t)md.m, md.hneg2);
+                        w0[h] = res_pair(zz.x, zz.y, m0.wlo, m0.whi, m0.cbias, m0.magic, (uint32_t)m0.m, m0.hneg2);
+                        w1[h] = res_pair(zz.x, zz.y, m1.wlo, m1.whi, m1.cbias, m1.magic, (uint32_t)m1.m, m1.hneg2);
                     }
-                    *reinterpret_cast<uint4 *>(a_base + it * 2 * 128) = make_uint4(w[0], w[1], w[2], w[3]);
+                    *reinterpret_cast<uint4 *>(a_slot + it * 2 * 128) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+                    *reinterpret_cast<uint4 *>(a_slot + A_STAGE + it * 2 * 128) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 // the warp barrier orders every lane's raw reads and residue writes before lane 0's
                 // release of the raw slot and the operand slot
                 __syncwarp();
                 if (lane == 0) {
-                    mbar_arrive(&bars->rawempty[warp]);
-                    mbar_arrive(&bars->full[warp]);
+                    mbar_arrive(&bars->rawempty[rslot]);
+                    mbar_arrive(&bars->full[slot]);
                 }
                 if (!go()) { alive = false; break; }
             }
@@ -395,34 +406,31 @@ __global__ void __launch_bounds__(NCONV_WARPS * 32 + 96, 1) k_crt_tc(const __gri
         uint32_t s = 0, u = 0;
         uint32_t acc_commits = 0;
         bool wait_free = false;
-        // descriptors of ring slot 0; slot s adds s * stage / 16 to the start-address field
+        // descriptors of slot 0, modulus 0; slot s, modulus j adds (2 s + j) stage / 16 to the
+        // start-address field
         const uint64_t adesc0 = sdesc(smem_u32(sA), 2048, 128, 0), bdesc0 = sdesc(smem_u32(sB), 16, 256, 6);
-        // slabs go in steps of CB: one pass of barrier waits, then CB MMAs, each committing its
-        // slot's "empty" barrier
         for (uint64_t tile = blockIdx.x; tile < p.n_tiles && !*abort_flag; tile += gridDim.x) {
+            const bool two = tile_coord(p, tile).two;
             bool alive = true;
             uint32_t to_flush = FLUSH_SLABS;                             // slabs to the next reduction
-            for (uint64_t kt = 0; kt < nk && alive; kt += CB) {
-                const int nbt = (nk - kt) < (uint64_t)CB ? (int)(nk - kt) : CB;
+            for (uint64_t kt = 0; kt < nk; ++kt) {
                 if (wait_free) {
                     if (!mbar_wait(&bars->acc_free, (acc_commits - 1) & 1, abort_flag)) { alive = false; break; }
                     wait_free = false;
                 }
-                for (int b = 0; b < nbt && alive; ++b) {
-                    const uint32_t sb = s + b < S ? s + b : s + b - S, ub = s + b < S ? u : u + 1;
-                    alive = mbar_wait(&bars->full[sb], ub & 1, abort_flag) && mbar_wait(&bars->bfull[sb], ub & 1, abort_flag);
+                if (!mbar_wait(&bars->full[s], u & 1, abort_flag) || !mbar_wait(&bars->bfull[s], u & 1, abort_flag)) {
+                    alive = false;
+                    break;
                 }
-                if (!alive) break;
                 tc_fence_after();
-                for (int b = 0; b < nbt; ++b) {
-                    const uint32_t sb = s + b < S ? s + b : s + b - S;
-                    umma(tmem, adesc0 + (uint64_t)(sb * (A_STAGE >> 4)), bdesc0 + (uint64_t)(sb * (B_STAGE >> 4)),
-                         (kt + b) > 0 ? 1u : 0u);
-                    umma_commit(&bars->empty[sb]);
-                }
-                s += nbt; if (s >= S) { s -= S; ++u; }
-                to_flush -= nbt;
-                if (to_flush == 0 || kt + nbt == nk) {                   // a reduction point closes a step
+                const uint32_t acc = kt > 0 ? 1u : 0u;
+                umma(tmem, adesc0 + (uint64_t)(2 * s * (A_STAGE >> 4)), bdesc0 + (uint64_t)(2 * s * (B_STAGE >> 4)), acc);
+                if (two)
+                    umma(tmem + 256, adesc0 + (uint64_t)((2 * s + 1) * (A_STAGE >> 4)),
+                         bdesc0 + (uint64_t)((2 * s + 1) * (B_STAGE >> 4)), acc);
+                umma_commit(&bars->empty[s]);
+                if (++s == S) { s = 0; ++u; }
+                if (--to_flush == 0 || kt + 1 == nk) {                   // a reduction point
                     umma_commit(&bars->acc_full);
                     ++acc_commits;
                     wait_free = true;
@@ -464,9 +472,12 @@ __global__ void __launch_bounds__(NCONV_WARPS * 32 + 96, 1) k_crt_tc(const __gri
             bool alive = true;
             for (uint64_t kt = 0; kt < nk; ++kt) {
                 if (u > 0 && !mbar_wait(&bars->empty[s], (u - 1) & 1, abort_flag)) { alive = false; break; }
-                mbar_expect_tx(&bars->bfull[s], B_STAGE);
-                tma_load_4d(smem_u32(sB + s * B_STAGE), &p.tmB, (int)(kt * KS), (int)(p.n0 + nb), (int)tc.mi, (int)tc.l,
-                            &bars->bfull[s]);
+                mbar_expect_tx(&bars->bfull[s], tc.two ? 2 * B_STAGE : B_STAGE);
+                unsigned char *b_s = sB + s * 2 * B_STAGE;
+                tma_load_4d(smem_u32(b_s), &p.tmB, (int)(kt * KS), (int)(p.n0 + nb), (int)tc.mi, (int)tc.l, &bars->bfull[s]);
+                if (tc.two)
+                    tma_load_4d(smem_u32(b_s + B_STAGE), &p.tmB, (int)(kt * KS), (int)(p.n0 + nb), (int)tc.mi + 1, (int)tc.l,
+                                &bars->bfull[s]);
                 ++issued;
                 if (++s == S) { s = 0; ++u; }
             }
@@ -507,9 +518,7 @@ EncodeTiled encode_fn() {
 namespace icm {
 
 cudaError_t crt_tc_set_attributes() {
-    cudaError_t e = cudaFuncSetAttribute(k_crt_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_crt_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    return e;
+    return cudaFuncSetAttribute(k_crt_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
 }
 
 // The tcgen05 path needs an even K (tensor-map row strides are multiples of 16 bytes); the caller
@@ -526,7 +535,7 @@ uint32_t device_status(bool clear) {
     return v;
 }
 
-cudaError_t launch_ppmm_crt_tc(int variant, const I8Consts &k, const ChunkTab &tab, const void *Bp, uint64_t N, uint64_t K,
+cudaError_t launch_ppmm_crt_tc(const I8Consts &k, const ChunkTab &tab, const void *Bp, uint64_t N, uint64_t K,
                                uint64_t Kp, void *scratch, cudaStream_t st) {
     const uint64_t Mall = tab.row0[tab.n];
     if (Mall == 0 || N == 0) return cudaSuccess;
@@ -564,17 +573,17 @@ cudaError_t launch_ppmm_crt_tc(int variant, const I8Consts &k, const ChunkTab &t
     a.R = reinterpret_cast<uint8_t *>(scratch);
     a.N = N; a.K = K;
     a.n_mod = k.n_mod;
+    a.n_pair = (k.n_mod + 1) / 2;
     for (uint32_t i = 0; i < k.n_mod; ++i)
         a.md[i] = TcMod{k.mod[i], k.wlo[i], k.whi[i], k.cbias[i], k.magic[i], k.hneg2[i], k.inv_m[i]};
     for (uint64_t n0 = 0; n0 < N; n0 += NCHUNK) {
         const uint64_t nch = std::min<uint64_t>(NCHUNK, N - n0);
         a.n0 = n0; a.nch = nch;
         a.n_ntile = (uint32_t)((nch + BN - 1) / BN);
-        a.n_tiles = (uint64_t)k.n_limbs * tab.mt0[tab.n] * k.n_mod * a.n_ntile;
+        a.n_tiles = (uint64_t)k.n_limbs * tab.mt0[tab.n] * a.n_pair * a.n_ntile;
         const uint64_t grid = std::min<uint64_t>(a.n_tiles, (uint64_t)sms);
         if (grid == 0) continue;
-        if (variant == ICM_CRT_TCGEN05_C4) k_crt_tc<4><<<(unsigned)grid, NCONV_WARPS * 32 + 96, SMEM_BYTES, st>>>(a);
-        else k_crt_tc<1><<<(unsigned)grid, NCONV_WARPS * 32 + 96, SMEM_BYTES, st>>>(a);
+        k_crt_tc<<<(unsigned)grid, NWC * 32 + 96, SMEM_BYTES, st>>>(a);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         e = launch_crt_combine(k, tab, scratch, N, n0, nch, st);

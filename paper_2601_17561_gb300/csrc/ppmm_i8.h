@@ -53,14 +53,13 @@ cudaError_t launch_ppmm_crt_grouped(bool f16, int bn, const I8Consts &k, const C
 cudaError_t crt_set_attributes();
 // Kernel variants of the CRT product (the column tile of the mma.sync kernel, or the tcgen05
 // kernel for the fp16 form on the balanced-digit database).
-#define ICM_CRT_TCGEN05 1        // tcgen05, one MMA per pass of the MMA thread over its barriers
-#define ICM_CRT_TCGEN05_C4 2     // tcgen05, four MMAs per pass
-inline bool crt_tc_variant(int v) { return v == ICM_CRT_TCGEN05 || v == ICM_CRT_TCGEN05_C4; }
+#define ICM_CRT_TCGEN05 1
+inline bool crt_tc_variant(int v) { return v == ICM_CRT_TCGEN05; }
 cudaError_t launch_crt_combine(const I8Consts &k, const ChunkTab &tab, const void *scratch, uint64_t N, uint64_t n0,
                                uint64_t nch, cudaStream_t st);
 cudaError_t crt_tc_set_attributes();
 bool crt_tc_supported(uint64_t K);
-cudaError_t launch_ppmm_crt_tc(int variant, const I8Consts &k, const ChunkTab &tab, const void *Bp, uint64_t N, uint64_t K, uint64_t Kp,
+cudaError_t launch_ppmm_crt_tc(const I8Consts &k, const ChunkTab &tab, const void *Bp, uint64_t N, uint64_t K, uint64_t Kp,
                                void *scratch, cudaStream_t st);
 uint32_t device_status(bool clear);
 // small-modulus CRT forms (int8 or fp16 operands): query residue planes, two-phase product

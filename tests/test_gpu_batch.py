@@ -72,7 +72,7 @@ def test_autotune_keeps_results(setup):
     eng, dbs = setup["eng"], setup["dbs"]
     q = eng.prepare(setup["ct"], 3, "f16_crt")
     best, ms = eng.autotune(dbs, q)
-    assert best in (128, 256, 1, 2) and all(m > 0 for m in ms)
+    assert best in (128, 256, 1) and all(m > 0 for m in ms)
     outs = eng.match_batch(dbs, q)
     torch.cuda.synchronize()
     for s, ref in zip(outs, setup["ref"]):
