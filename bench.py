@@ -409,8 +409,9 @@ def main():
     elif args.form in ("i8_digits", "i8_crt", "f16_crt"):
         kp = (K + 31) // 32 * 32
         esz = 2 if args.form == "f16_crt" else 1
+        # CRT moduli: the match scratch holds L x r x min(N, 512) x M residue bytes
         pairs = 64 if args.form == "i8_digits" else \
-            int((C.icm_query_op_bytes(eng.ctx, 1, f) - L * 31 * K * 8) // (L * 31 * kp * esz))
+            int(eng.match_workspace(db, N_EYES, args.form).numel() // (L * min(n_cols, 512) * M))
         ops = 2.0 * pairs * M * n_cols * kp * L
         if args.form == "f16_crt":
             # fp16 and bf16 share the dense tensor rate; the CCMM launch runs for seconds, so the

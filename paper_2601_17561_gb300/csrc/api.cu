@@ -350,8 +350,7 @@ icm_status icm_query_op_bytes(const icm_ctx *c, size_t n_eyes, icm_form form, si
         case ICM_FORM_F16_CRT: {
             if (form != ICM_FORM_I8_DIGITS && !c->i8_crt_ok) return fail(ICM_EBOUND, "CRT form unavailable for these primes / K");
             const uint32_t P = form == ICM_FORM_I8_DIGITS ? 8 : c->i8_crt.n_mod;
-            const size_t esz = form == ICM_FORM_F16_CRT ? 2 : 1;
-            *bytes = n * 8 + (size_t)c->p.n_limbs * P * n_eyes * c->p.rho * i8_kpad(c->K) * esz;
+            *bytes = n * 8 + crt_plane_bytes(form == ICM_FORM_F16_CRT, c->p.n_limbs, P, n_eyes * c->p.rho, i8_kpad(c->K));
             return ICM_OK;
         }
         default: return fail(ICM_EUNSUPPORTED, "form not built");
@@ -533,7 +532,7 @@ icm_status icm_ppmm_workspace_bytes(icm_form form, uint32_t n_limbs, size_t M, s
             const uint64_t qworst = (1ull << 60) - 1;
             const uint32_t P = i8_planes(pf, &qworst, 1, K);
             if (!P) return fail(ICM_EBOUND, "CRT form unavailable for this K");
-            *bytes = (size_t)n_limbs * P * N * i8_kpad(K) * (form == ICM_FORM_F16_CRT ? 2 : 1);
+            *bytes = crt_plane_bytes(form == ICM_FORM_F16_CRT, n_limbs, P, N, i8_kpad(K));
             if (form != ICM_FORM_I8_DIGITS) *bytes += 256 + crt_scratch_bytes(n_limbs, P, N, M);
             return ICM_OK;
         }
@@ -574,7 +573,7 @@ icm_status icm_ppmm(icm_form form, const uint64_t *q, uint32_t n_limbs, const ui
             const char *why = "";
             if (!make_i8_consts(ICM_FORM_I8_CRT, qv.data(), qv.size(), K, k, &why)) return fail(ICM_EBOUND, why);
             const bool f16 = form == ICM_FORM_F16_CRT;
-            const size_t pl = (size_t)n_limbs * k.n_mod * N * i8_kpad(K) * (f16 ? 2 : 1);
+            const size_t pl = crt_plane_bytes(f16, n_limbs, k.n_mod, N, i8_kpad(K));
             const size_t sc = crt_scratch_bytes(n_limbs, k.n_mod, N, M);
             if ((pl || sc) && (!dev_ws || ws_bytes < align256(pl) + sc)) return fail(ICM_ENOMEM, "workspace too small");
             e = launch_crt_planes(f16, k, dev_B, dev_ws, N, K, i8_kpad(K), (cudaStream_t)stream);

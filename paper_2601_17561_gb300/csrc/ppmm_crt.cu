@@ -4,12 +4,13 @@
 // (the same residues held exactly as fp16, mma.sync m16n8k16 f16 -> f32; GB300 issues fp16 tensor
 // products at about four times its int8 rate).
 //
-// For r pairwise-coprime moduli m_i <= 256 with product M > 2^9 K ((q-1)/2)^2:
+// For r pairwise-coprime odd moduli m_i < 256 with product M > 2^9 K ((q-1)/2)^2:
 //  phase 1 (one block per limb, modulus, 128-row tile and column tile): c_i = C mod m_i with
-//    C = sum_k a[k] b[k] over the centred residues a = A mod m_i, b = B mod m_i (|x| <= 128) of
+//    C = sum_k a[k] b[k] over the centred residues a = A mod m_i, b = B mod m_i (|x| <= 127) of
 //    the centred lifts of A and B.  int8: int32 accumulation is exact (K 2^14 < 2^31).  fp16:
-//    products <= 2^14 are exact in fp32 and the fp32 sum stays an exact integer below 2^24, so it
-//    is reduced modulo m_i every 512 columns of K (512 * 2^14 + 128 < 2^24).  c_i goes to a byte
+//    products <= 127^2 are exact in fp32 and the fp32 sum stays an exact integer below 2^24, so it
+//    is reduced modulo m_i every 1024 columns of K (1024 * 127^2 + 1.5 * 255 < 2^24; a reduction
+//    leaves |x| <= 1.5 m_i because the rounded quotient may be off by one).  c_i goes to a byte
 //    scratch.
 //  phase 2 (one thread per output): C mod q = sum_i y_i (M/m_i mod q) - kappa (M mod q) with
 //    y_i = c_i (M/m_i)^-1 mod m_i and kappa = round(sum_i y_i / m_i) (|C| / M < 2^-9, so fp32
@@ -32,12 +33,12 @@
 
 namespace {
 
-constexpr int BM = 128, KS = 32, NT = 256, FLUSH = 512;
+constexpr int BM = 128, KS = 32, NT = 256, FLUSH = 1024;
 constexpr uint64_t NCHUNK = 512;            // columns per phase-1/phase-2 round
 
 struct P1Args {
     icm::ChunkTab tab;       // database chunks: A_c [L][M_c][K], scratch row offsets, row-tile offsets
-    const void *Bp;          // [L][r][N][Kp] int8 or fp16 planes
+    const void *Bp;          // residue planes: int8 [L][r][N][Kp], or fp16 tiled (crt_f16_off)
     uint8_t *R;              // [L][r][nch][sum M_c] scratch
     uint64_t N, K, Kp, n0, nch;
     uint32_t n_ntile;
@@ -136,7 +137,10 @@ __global__ void __launch_bounds__(NT, 1) k_crt_p1(P1Args p) {
     const float inv_m = p.k.inv_m[mi];
     const uint64_t q = p.k.q[l];
     const uint64_t *Al = p.tab.A[c] + (size_t)l * M * K;
-    const unsigned char *Bl = reinterpret_cast<const unsigned char *>(p.Bp) + (((size_t)l * r + mi) * N + p.n0) * Kp * ESZ;
+    // int8 planes [L][r][N][Kp] from the round's first column; fp16 planes in 256-column tiles
+    const unsigned char *Bl = reinterpret_cast<const unsigned char *>(p.Bp) +
+                              (F16 ? ((size_t)l * r + mi) * icm::crt_f16_ncols(N) * Kp * ESZ
+                                   : (((size_t)l * r + mi) * N + p.n0) * Kp * ESZ);
 
     AccT acc[4][NT8][4];
 #pragma unroll
@@ -179,7 +183,9 @@ __global__ void __launch_bounds__(NT, 1) k_crt_p1(P1Args p) {
         for (int e = 0; e < (BN * CH) / NT; ++e) {
             const int idx = tid + e * NT, col = idx / CH, ch = idx % CH;
             const bool ok = p.n0 + nb + col < N && nb + col < p.nch;
-            const unsigned char *src = Bl + (ok ? ((nb + col) * Kp + k0) * ESZ + ch * 16 : 0);
+            const uint64_t off = F16 ? icm::crt_f16_off(p.n0 + nb + col, k0 + ch * 8, Kp) * 2
+                                     : ((nb + col) * Kp + k0) * ESZ + ch * 16;
+            const unsigned char *src = Bl + (ok ? off : 0);
             cp_async16(smem_u32(sB + (size_t)st * BN * LDB + col * LDB + ch * 16), src, ok);
         }
         asm volatile("cp.async.commit_group;");
@@ -289,10 +295,9 @@ __global__ void __launch_bounds__(256) k_crt_combine(P2Args p) {
     p.tab.C[c][((size_t)l * p.N + p.n0 + col) * M + row] = sub_mod(S, mulmod_shoup(kappa, p.k.Mq[l], p.k.Mqs[l], q), q);
 }
 
-// Residue planes of the query operand: [L][r][N][Kp] (int8 or fp16), zero padded.
-template <bool F16>
-__global__ void __launch_bounds__(256) k_crt_planes(const uint64_t *op, void *planes, uint64_t N, uint64_t K, uint64_t Kp,
-                                                    icm::I8Consts k) {
+// int8 residue planes of the query operand: [L][r][N][Kp], zero padded.
+__global__ void __launch_bounds__(256) k_crt_planes_i8(const uint64_t *op, int8_t *planes, uint64_t N, uint64_t K,
+                                                       uint64_t Kp, icm::I8Consts k) {
     const uint32_t l = blockIdx.y;
     const uint32_t r = k.n_mod;
     const uint64_t q = k.q[l];
@@ -300,11 +305,36 @@ __global__ void __launch_bounds__(256) k_crt_planes(const uint64_t *op, void *pl
     for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t j = idx / Kp, kk = idx % Kp;
         const uint64_t v = kk < K ? op[((size_t)l * N + j) * K + kk] : 0;
+        for (uint32_t i = 0; i < r; ++i)
+            planes[((size_t)l * r + i) * total + idx] = (int8_t)crt_residue(v, q, k.mod[i], k.wlo[i], k.whi[i], k.inv_m[i]);
+    }
+}
+
+// fp16 residue planes in the tiled layout of crt_f16_off (zero padded in K and in the columns
+// of the last 256-column tile).  One thread per (column, 8 consecutive k): it reads 64 bytes of
+// the operand and writes one 16-byte core-matrix row per modulus; consecutive threads take
+// consecutive columns, so their stores fill contiguous memory.
+__global__ void __launch_bounds__(256) k_crt_planes_f16(const uint64_t *op, __half *planes, uint64_t N, uint64_t K,
+                                                        uint64_t Kp, icm::I8Consts k) {
+    const uint32_t l = blockIdx.y;
+    const uint32_t r = k.n_mod;
+    const uint64_t q = k.q[l];
+    const uint64_t Np = icm::crt_f16_ncols(N), total = Np * (Kp / 8);
+    for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t j = idx % Np, k0 = (idx / Np) * 8;
+        uint64_t v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = (j < N && k0 + e < K) ? op[((size_t)l * N + j) * K + k0 + e] : 0;
+        const uint64_t o = icm::crt_f16_off(j, k0, Kp);
         for (uint32_t i = 0; i < r; ++i) {
-            const int res = crt_residue(v, q, k.mod[i], k.wlo[i], k.whi[i], k.inv_m[i]);
-            const size_t o = ((size_t)l * r + i) * total + idx;
-            if (F16) reinterpret_cast<__half *>(planes)[o] = __int2half_rn(res);
-            else reinterpret_cast<int8_t *>(planes)[o] = (int8_t)res;
+            uint32_t w[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                __half2 h = __halves2half2(__int2half_rn(crt_residue(v[2 * e], q, k.mod[i], k.wlo[i], k.whi[i], k.inv_m[i])),
+                                           __int2half_rn(crt_residue(v[2 * e + 1], q, k.mod[i], k.wlo[i], k.whi[i], k.inv_m[i])));
+                w[e] = *reinterpret_cast<uint32_t *>(&h);
+            }
+            *reinterpret_cast<uint4 *>(planes + ((size_t)l * r + i) * Np * Kp + o) = make_uint4(w[0], w[1], w[2], w[3]);
         }
     }
 }
@@ -367,10 +397,11 @@ bool make_chunk_tab(const uint64_t *const *A, uint64_t *const *C, const uint64_t
 cudaError_t launch_crt_planes(bool f16, const I8Consts &k, const uint64_t *op, void *planes, uint64_t N, uint64_t K,
                               uint64_t Kp, cudaStream_t st) {
     if (N == 0 || Kp == 0) return cudaSuccess;
-    const uint64_t total = N * Kp;
+    if (Kp % 16 || (f16 && reinterpret_cast<uintptr_t>(planes) % 16)) return cudaErrorInvalidValue;
+    const uint64_t total = f16 ? crt_f16_ncols(N) * (Kp / 8) : N * Kp;
     const unsigned blocks = (unsigned)std::min<uint64_t>((total + 255) / 256, 152u * 32u);
-    if (f16) k_crt_planes<true><<<dim3(blocks, k.n_limbs), 256, 0, st>>>(op, planes, N, K, Kp, k);
-    else k_crt_planes<false><<<dim3(blocks, k.n_limbs), 256, 0, st>>>(op, planes, N, K, Kp, k);
+    if (f16) k_crt_planes_f16<<<dim3(blocks, k.n_limbs), 256, 0, st>>>(op, reinterpret_cast<__half *>(planes), N, K, Kp, k);
+    else k_crt_planes_i8<<<dim3(blocks, k.n_limbs), 256, 0, st>>>(op, reinterpret_cast<int8_t *>(planes), N, K, Kp, k);
     return cudaGetLastError();
 }
 

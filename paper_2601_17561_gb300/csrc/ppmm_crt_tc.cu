@@ -3,8 +3,9 @@
 // for one (limb, database chunk, 128-row tile, pair of moduli m_i, m_i+1, 256-column tile) it
 // computes c_i = (sum_k a[k] b[k]) mod m_i over residues held exactly in fp16 (|r| <= 128),
 // accumulating in fp32 TMEM (one 256-column accumulator per modulus, all 512 columns) and
-// reducing the accumulators modulo m_i every 512 columns of K so that they stay exact integers
-// below 2^24; c_i goes to the byte scratch that phase 2 (k_crt_combine) recombines.
+// reducing the accumulators modulo m_i every 1024 columns of K so that they stay exact integers
+// below 2^24 (odd moduli: |r| <= 127, 1024 * 127^2 + 1.5 * 255 < 2^24); c_i goes to the byte
+// scratch that phase 2 (k_crt_combine) recombines.
 //
 // Pairing the moduli halves the shared-memory traffic and conversion overhead per modulus: the
 // raw database slab is loaded and read once for two MMAs.
@@ -13,9 +14,11 @@
 //  * Raw producer: one TMA load per slab of the 128 x 16 balanced-digit storage words of the
 //    database rows (128-byte swizzle: the 16-byte chunk c of row r sits at chunk c ^ (r mod 8)),
 //    into a ring of RS raw slots ("rawfull" / "rawempty" mbarriers).
-//  * Query producer: per slab, one TMA load per modulus of the 256 x 16 fp16 residue planes of
-//    the query (32-byte swizzle, the canonical K-major SW32 layout of the MMA) into the B half of a
-//    ring of S operand slots ("bfull"; released by the MMA through "empty").
+//  * Query producer: per slab, one bulk copy per modulus of the query's 8 KB residue block (the
+//    planes are stored pre-tiled in the MMA's K-major core-matrix layout, so a 256 x 16 operand is
+//    one contiguous block: 64 requests of 128 bytes, where a row-by-row tensor load of 32-byte rows
+//    needs 256) into the B half of a ring of S operand slots ("bfull"; released by the MMA through
+//    "empty").
 //  * Converters: warps w and w + 4 own operand slot w and raw slots w and w + 4, and convert every
 //    slab g with g mod 4 = w, 64 rows each: 8 consecutive storage words of a row become 8 fp16
 //    residues per modulus (two dp4a, a multiply-high division and an f16x2 add per pair; no
@@ -23,7 +26,7 @@
 //    x 16-byte core matrices).  Every quarter-warp reads 8 distinct bank groups of the swizzled
 //    raw slot and writes 128 contiguous bytes.
 //  * MMA: one elected thread issues one tcgen05.mma (M = 128, N = 256, K = 16) per modulus and
-//    slab and commits to the slot's "empty" mbarrier.  Every 32 slabs and at the end of a tile it
+//    slab and commits to the slot's "empty" mbarrier.  Every 64 slabs and at the end of a tile it
 //    commits to "acc_full"; the converters (warps w mod 4 = q serve TMEM lane quarter q, warps 0-3
 //    the first accumulator and 4-7 the second) reduce the accumulators in place (tcgen05.ld / st)
 //    or write the final residues, and arrive on "acc_free".
@@ -45,7 +48,7 @@ constexpr int BM = 128, BN = 256, KS = 16;
 constexpr int NWC = 8;                            // converter warps (two per operand slot)
 constexpr int S = 4;                              // operand slots (A residues + B planes, 2 moduli)
 constexpr int RS = 8;                             // raw database slots
-constexpr int FLUSH_SLABS = 32;                   // 512 columns of K between reductions
+constexpr int FLUSH_SLABS = 64;                   // 1024 columns of K between reductions
 constexpr int A_STAGE = BM * KS * 2;              // 4 KB per modulus
 constexpr int B_STAGE = BN * KS * 2;              // 8 KB per modulus
 constexpr int RAW_STAGE = BM * KS * 8;            // 16 KB
@@ -70,7 +73,8 @@ struct TcMod {
 
 struct TcArgs {
     CUtensorMap tmA[ICM_MAX_CHUNKS];  // per chunk: [L][M_c][K] u64, box 16 x 128, 128-byte swizzle
-    CUtensorMap tmB;                  // [L][r][N][Kp] fp16, box 16 x 256, 32-byte swizzle
+    const unsigned char *Bt;          // fp16 planes, tiled (crt_f16_off): one 8 KB block per (tile, slab)
+    uint64_t Kp, plane;               // padded K; bytes of one (limb, modulus) plane
     icm::ChunkTab tab;
     uint8_t *R;                       // [L][r][nch][sum M_c]
     uint64_t N, K, n0, nch;
@@ -136,11 +140,11 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map
                  :: "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
                  : "memory");
 }
-__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
-                                            uint64_t *bar) {
-    asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
-                 :: "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
-                 : "memory");
+
+// Bulk copy of `bytes` contiguous bytes (16-byte aligned) into this block's shared memory.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(dst), "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar)) : "memory");
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -148,7 +152,8 @@ __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::
 
 // Shared memory matrix descriptor: start address >> 4 [0,14), leading byte offset >> 4 [16,30),
 // stride byte offset >> 4 [32,46), version 1 [46,48), base offset 0, swizzle mode [61,64)
-// (0 none, 6 32-byte).
+// (0: none).  K-major without swizzle: 8-row x 16-byte core matrices, the leading offset steps
+// from k 0-7 to k 8-15, the stride offset from one group of 8 rows to the next.
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo, uint32_t swz) {
     return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | ((uint64_t)swz << 61);
@@ -408,7 +413,7 @@ __global__ void __launch_bounds__(NWC * 32 + 96, 1) k_crt_tc(const __grid_consta
         bool wait_free = false;
         // descriptors of slot 0, modulus 0; slot s, modulus j adds (2 s + j) stage / 16 to the
         // start-address field
-        const uint64_t adesc0 = sdesc(smem_u32(sA), 2048, 128, 0), bdesc0 = sdesc(smem_u32(sB), 16, 256, 6);
+        const uint64_t adesc0 = sdesc(smem_u32(sA), 2048, 128, 0), bdesc0 = sdesc(smem_u32(sB), 4096, 128, 0);
         for (uint64_t tile = blockIdx.x; tile < p.n_tiles && !*abort_flag; tile += gridDim.x) {
             const bool two = tile_coord(p, tile).two;
             bool alive = true;
@@ -468,16 +473,16 @@ __global__ void __launch_bounds__(NWC * 32 + 96, 1) k_crt_tc(const __grid_consta
         uint64_t issued = 0;
         for (uint64_t tile = blockIdx.x; tile < p.n_tiles && !*abort_flag; tile += gridDim.x) {
             const TileCoord tc = tile_coord(p, tile);
-            const uint64_t nb = (uint64_t)tc.nt * BN;
+            // first block of this (limb, modulus, 256-column tile); the next modulus is one plane on
+            const unsigned char *b_src = p.Bt + ((size_t)tc.l * p.n_mod + tc.mi) * p.plane +
+                                         (size_t)((p.n0 + (uint64_t)tc.nt * BN) / BN) * (p.Kp / KS) * B_STAGE;
             bool alive = true;
             for (uint64_t kt = 0; kt < nk; ++kt) {
                 if (u > 0 && !mbar_wait(&bars->empty[s], (u - 1) & 1, abort_flag)) { alive = false; break; }
                 mbar_expect_tx(&bars->bfull[s], tc.two ? 2 * B_STAGE : B_STAGE);
                 unsigned char *b_s = sB + s * 2 * B_STAGE;
-                tma_load_4d(smem_u32(b_s), &p.tmB, (int)(kt * KS), (int)(p.n0 + nb), (int)tc.mi, (int)tc.l, &bars->bfull[s]);
-                if (tc.two)
-                    tma_load_4d(smem_u32(b_s + B_STAGE), &p.tmB, (int)(kt * KS), (int)(p.n0 + nb), (int)tc.mi + 1, (int)tc.l,
-                                &bars->bfull[s]);
+                bulk_load(smem_u32(b_s), b_src + kt * B_STAGE, B_STAGE, &bars->bfull[s]);
+                if (tc.two) bulk_load(smem_u32(b_s + B_STAGE), b_src + p.plane + kt * B_STAGE, B_STAGE, &bars->bfull[s]);
                 ++issued;
                 if (++s == S) { s = 0; ++u; }
             }
@@ -559,16 +564,11 @@ cudaError_t launch_ppmm_crt_tc(const I8Consts &k, const ChunkTab &tab, const voi
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return cudaErrorInvalidValue;
     }
-    // query planes: [L][r][N][Kp] fp16 bits, box 16 columns of K x 256 rows
-    {
-        const cuuint64_t dims[4] = {Kp, N, k.n_mod, k.n_limbs};
-        const cuuint64_t strides[3] = {Kp * 2, N * Kp * 2, (cuuint64_t)k.n_mod * N * Kp * 2};
-        const cuuint32_t box[4] = {KS, BN, 1, 1}, estr[4] = {1, 1, 1, 1};
-        if (enc(&a.tmB, CU_TENSOR_MAP_DATA_TYPE_UINT16, 4, const_cast<void *>(Bp), dims, strides, box, estr,
-                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-            return cudaErrorInvalidValue;
-    }
+    // query planes: tiled fp16 blocks (crt_f16_off), 16-byte aligned for the bulk copies
+    if (reinterpret_cast<uintptr_t>(Bp) % 16) return cudaErrorInvalidValue;
+    a.Bt = reinterpret_cast<const unsigned char *>(Bp);
+    a.Kp = Kp;
+    a.plane = crt_f16_ncols(N) * Kp * 2;
     a.tab = tab;
     a.R = reinterpret_cast<uint8_t *>(scratch);
     a.N = N; a.K = K;

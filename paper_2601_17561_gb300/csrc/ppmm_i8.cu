@@ -12,7 +12,7 @@
 // is folded into the modular result R += (T mod q) (2^(8 s) mod q).
 //
 // CRT form (small-modulus RNS, as in the paper's own RNS of small moduli below 2^8): for r
-// pairwise-coprime moduli m_i <= 256 whose product M exceeds 2 K ((q-1)/2)^2 by 2^8, one int8 GEMM
+// pairwise-coprime odd moduli m_i < 256 whose product M exceeds 2 K ((q-1)/2)^2 by 2^8, one int8 GEMM
 // per modulus on the centred residues of x mod m_i gives c_i = C mod m_i exactly (K (2^7)^2 < 2^31),
 // and C mod q = sum_i y_i (M/m_i mod q) - kappa (M mod q) with y_i = c_i (M/m_i)^-1 mod m_i and
 // kappa = round(sum_i y_i / m_i) (C / M lies within 2^-8 of zero, so fp32 decides kappa exactly).
@@ -69,12 +69,11 @@ __device__ __forceinline__ void digits4(const uint64_t (&x)[4], uint64_t q, bool
     out[6] = __byte_perm(d01, d23, 0x5410); out[7] = __byte_perm(d01, d23, 0x7632);
 }
 
-// Centred residue (|r| <= 128) of x mod m from the 8 digits of x: x = sum_t d_t 256^t, so
+// Centred residue (|r| <= 127, m odd) of x mod m from the 8 digits of x: x = sum_t d_t 256^t, so
 // x = sum_t d_t w_t (mod m) with centred constants w_t = 256^t mod m; two dp4a give the sum.
 __device__ __forceinline__ int residue_from_digits(uint32_t dlo, uint32_t dhi, int wlo, int whi, int m, float inv_m) {
     int s = __dp4a((int)dlo, wlo, 0);
     s = __dp4a((int)dhi, whi, s);
-    if (m == 256) return (int)(int8_t)(s & 0xFF);
     int r = s - m * __float2int_rn((float)s * inv_m);
     const int h = (m - 1) >> 1;
     r = r > h ? r - m : (r < -h ? r + m : r);
@@ -296,8 +295,12 @@ int64_t inv_h(int64_t a, int64_t m) {
 }
 uint64_t shoup_h(uint64_t w, uint64_t q) { return (uint64_t)(((u128)w << 64) / q); }
 
-// Greedy: the largest pairwise-coprime integers <= 256, as many as the range needs.  Fills mods
-// and returns their count (0 if no set within ICM_MAX_MODULI covers the range); no allocation.
+// Greedy: the largest pairwise-coprime odd integers below 256, as many as the range needs.  Odd
+// moduli keep every centred residue within [-127, 127], so a product is at most 127^2 = 16,129
+// and 1024 products plus a reduced residue (|x| <= 1.5 m) stay below 2^24, the bound under which
+// the fp16 forms' fp32 sums are exact (leaving out 256 costs no modulus for 50- and 60-bit primes).
+// Fills mods and returns their count (0 if no set within ICM_MAX_MODULI covers the range); no
+// allocation.
 uint32_t crt_moduli(const uint64_t *q, size_t nq, uint64_t K, int (&mods)[ICM_MAX_MODULI]) {
     uint64_t qmax = 0;
     for (size_t i = 0; i < nq; ++i) qmax = q[i] > qmax ? q[i] : qmax;
@@ -305,7 +308,7 @@ uint32_t crt_moduli(const uint64_t *q, size_t nq, uint64_t K, int (&mods)[ICM_MA
     const double need = 1.0 + std::log2((double)(K ? K : 1)) + 2.0 * std::log2((double)((qmax - 1) / 2 + 1)) + 8.0;
     uint32_t n = 0;
     double have = 0;
-    for (int v = 256; v >= 3 && have < need && n < ICM_MAX_MODULI; --v) {
+    for (int v = 255; v >= 3 && have < need && n < ICM_MAX_MODULI; v -= 2) {
         bool ok = true;
         for (uint32_t i = 0; i < n; ++i) if (gcd_h((uint64_t)v, (uint64_t)mods[i]) != 1) { ok = false; break; }
         if (ok) { mods[n++] = v; have += std::log2((double)v); }
@@ -344,8 +347,7 @@ bool make_i8_consts(int form, const uint64_t *q, size_t nq, uint64_t K, I8Consts
         int w[8];
         for (int t = 0; t < 8; ++t) {
             int v = (int)powmod_h(256, (uint64_t)t, (uint64_t)m);
-            if (m == 256) v = (t == 0) ? 1 : 0;
-            else if (v > (m - 1) / 2) v -= m;              // centred
+            if (v > (m - 1) / 2) v -= m;                   // centred
             w[t] = v;
         }
         k.mod[i] = m;

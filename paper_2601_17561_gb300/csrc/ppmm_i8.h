@@ -62,6 +62,24 @@ bool crt_tc_supported(uint64_t K);
 cudaError_t launch_ppmm_crt_tc(const I8Consts &k, const ChunkTab &tab, const void *Bp, uint64_t N, uint64_t K, uint64_t Kp,
                                void *scratch, cudaStream_t st);
 uint32_t device_status(bool clear);
+// Residue planes of the query operand in the CRT forms.
+//  int8: [L][r][N][Kp], K contiguous.
+//  fp16: per (limb, modulus) the columns are grouped in tiles of 256 (N padded with zero columns)
+//  and K in slabs of 16; every (column tile, slab) pair is one contiguous 8 KB block holding the
+//  256 x 16 operand in the tensor cores' K-major layout without swizzle: the core matrices
+//  (8 columns x 8 consecutive k, 16 bytes per column) of k 0-7 for column groups 0..31, then those
+//  of k 8-15.  One bulk copy moves a block into shared memory as it is; blocks of consecutive
+//  slabs of a column tile are adjacent.
+constexpr uint64_t CRT_F16_TN = 256;
+__host__ __device__ inline uint64_t crt_f16_ncols(uint64_t N) { return (N + CRT_F16_TN - 1) / CRT_F16_TN * CRT_F16_TN; }
+inline uint64_t crt_plane_bytes(bool f16, uint32_t n_limbs, uint32_t n_mod, uint64_t N, uint64_t Kp) {
+    return f16 ? (uint64_t)n_limbs * n_mod * crt_f16_ncols(N) * Kp * 2 : (uint64_t)n_limbs * n_mod * N * Kp;
+}
+// fp16 element offset of (column j, k) within one (limb, modulus) plane of Kp columns of K
+__host__ __device__ __forceinline__ uint64_t crt_f16_off(uint64_t j, uint64_t k, uint64_t Kp) {
+    return ((j >> 8) * (Kp >> 4) + (k >> 4)) * 4096 + ((((k >> 3) & 1) * 32 + ((j & 255) >> 3)) * 8 + (j & 7)) * 8 +
+           (k & 7);
+}
 // small-modulus CRT forms (int8 or fp16 operands): query residue planes, two-phase product
 uint64_t crt_scratch_bytes(uint32_t n_limbs, uint32_t n_mod, uint64_t N, uint64_t M);
 cudaError_t launch_crt_planes(bool f16, const I8Consts &k, const uint64_t *op, void *planes, uint64_t N, uint64_t K,

@@ -49,7 +49,7 @@ extern "C" icm_status icm_ppmm_noalloc(icm_form form, const uint64_t *q, uint32_
     if (!make_i8_consts(ICM_FORM_I8_CRT, q, n_limbs, K, k, &why)) return api_fail(ICM_EBOUND, why);
     const bool f16 = form == ICM_FORM_F16_CRT;
     const uint64_t Kp = i8_kpad(K);
-    const size_t planes = (size_t)n_limbs * k.n_mod * N * Kp * (f16 ? 2 : 1);
+    const size_t planes = crt_plane_bytes(f16, n_limbs, k.n_mod, N, Kp);
     const size_t need = a256(planes) + crt_scratch_bytes(n_limbs, k.n_mod, N, M);
     if (need > ICM_NOALLOC_SCRATCH_BYTES)
         return api_fail(ICM_ENOMEM, "problem exceeds the 64 MiB static workspace of icm_ppmm_noalloc");
