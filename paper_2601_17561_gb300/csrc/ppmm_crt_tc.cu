@@ -1,35 +1,38 @@
 // Phase 1 of the fp16 small-modulus CRT product on the tcgen05 tensor cores (Blackwell 5th-gen
 // MMA with accumulators in tensor memory).  Same arithmetic as k_crt_p1<fp16> (ppmm_crt.cu):
-// for one (limb, database chunk, 128-row tile, pair of moduli m_i, m_i+1, 256-column tile) it
-// computes c_i = (sum_k a[k] b[k]) mod m_i over residues held exactly in fp16 (|r| <= 128),
-// accumulating in fp32 TMEM (one 256-column accumulator per modulus, all 512 columns) and
+// for one (limb, database chunk, 128-row tile, modulus m_i, 512-column round) it computes
+// c_i = (sum_k a[k] b[k]) mod m_i over residues held exactly in fp16 (|r| <= 127), accumulating
+// in fp32 TMEM (two 256-column accumulators, one per column tile, all 512 columns) and
 // reducing the accumulators modulo m_i every 1024 columns of K so that they stay exact integers
 // below 2^24 (odd moduli: |r| <= 127, 1024 * 127^2 + 1.5 * 255 < 2^24); c_i goes to the byte
 // scratch that phase 2 (k_crt_combine) recombines.
 //
-// Pairing the moduli halves the shared-memory traffic and conversion overhead per modulus: the
-// raw database slab is loaded and read once for two MMAs.
+// One modulus on 512 columns: each raw database slab is loaded and converted once for two MMAs
+// (N = 256 each) that share the converted operand, so every residue the converters compute
+// feeds 512 columns.  (Two moduli on 256 columns each read the raw slab as often but convert it
+// twice: the conversion, integer work on the CUDA cores, was what bounded that layout.)
 //
-// Block: 8 converter warps, 1 MMA warp, 2 TMA producer warps; K advances in slabs of 16.
+// Block: 16 converter warps, 1 MMA warp, 2 TMA producer warps; K advances in slabs of 16.
 //  * Raw producer: one TMA load per slab of the 128 x 16 balanced-digit storage words of the
 //    database rows (128-byte swizzle: the 16-byte chunk c of row r sits at chunk c ^ (r mod 8)),
 //    into a ring of RS raw slots ("rawfull" / "rawempty" mbarriers).
 //  * Query producer: per slab, one bulk copy per modulus of the query's 8 KB residue block (the
 //    planes are stored pre-tiled in the MMA's K-major core-matrix layout, so a 256 x 16 operand is
 //    one contiguous block: 64 requests of 128 bytes, where a row-by-row tensor load of 32-byte rows
-//    needs 256) into the B half of a ring of S operand slots ("bfull"; released by the MMA through
-//    "empty").
-//  * Converters: warps w and w + 4 own operand slot w and raw slots w and w + 4, and convert every
-//    slab g with g mod 4 = w, 64 rows each: 8 consecutive storage words of a row become 8 fp16
-//    residues per modulus (two dp4a, a multiply-high division and an f16x2 add per pair; no
+//    needs 256) for each of the two column tiles into the B half of a ring of S operand slots
+//    ("bfull"; released by the MMA through "empty").
+//  * Converters: warps w, w + 4, w + 8 and w + 12 own operand slot w and raw slots w and w + 4, and
+//    convert every slab g with g mod 4 = w, 32 rows each: 8 consecutive storage words of a row become 8 fp16
+//    residues (two dp4a and a multiply-high division per residue, an f16x2 add per pair; no
 //    conversion-pipe instructions), written to the A half of the slot (K-major, no swizzle, 8-row
 //    x 16-byte core matrices).  Every quarter-warp reads 8 distinct bank groups of the swizzled
-//    raw slot and writes 128 contiguous bytes.
-//  * MMA: one elected thread issues one tcgen05.mma (M = 128, N = 256, K = 16) per modulus and
+//    raw slot and writes 128 contiguous bytes.  The conversion is latency-bound integer work, so
+//    four warps per scheduler (rather than two) keep the integer pipes fed.
+//  * MMA: one elected thread issues one tcgen05.mma (M = 128, N = 256, K = 16) per column tile and
 //    slab and commits to the slot's "empty" mbarrier.  Every 64 slabs and at the end of a tile it
-//    commits to "acc_full"; the converters (warps w mod 4 = q serve TMEM lane quarter q, warps 0-3
-//    the first accumulator and 4-7 the second) reduce the accumulators in place (tcgen05.ld / st)
-//    or write the final residues, and arrive on "acc_free".
+//    commits to "acc_full"; the converters (warp w serves TMEM lane quarter w mod 4 and columns
+//    128 floor(w / 4) .. + 127 of the 512 accumulator columns) reduce the accumulators in place
+//    (tcgen05.ld / st) or write the final residues, and arrive on "acc_free".
 //
 // Every wait is bounded by %globaltimer (2 s); on expiry the block records ICM_DEV_TIMEOUT in the
 // device status word, stops issuing work, waits (bounded) for its own MMAs and TMA loads, and
@@ -45,24 +48,28 @@
 namespace {
 
 constexpr int BM = 128, BN = 256, KS = 16;
-constexpr int NWC = 8;                            // converter warps (two per operand slot)
-constexpr int S = 4;                              // operand slots (A residues + B planes, 2 moduli)
+constexpr int NWC = 16;                           // converter warps (four per operand slot)
+constexpr int S = 4;                              // operand slots (A residues + B planes of 2 column tiles)
 constexpr int RS = 8;                             // raw database slots
 constexpr int FLUSH_SLABS = 64;                   // 1024 columns of K between reductions
-constexpr int A_STAGE = BM * KS * 2;              // 4 KB per modulus
-constexpr int B_STAGE = BN * KS * 2;              // 8 KB per modulus
+constexpr int A_STAGE = BM * KS * 2;              // 4 KB
+constexpr int B_STAGE = BN * KS * 2;              // 8 KB per column tile
 constexpr int RAW_STAGE = BM * KS * 8;            // 16 KB
 constexpr uint32_t TMEM_COLS = 512;               // two 256-column fp32 accumulators
 constexpr uint64_t WAIT_NS = 2000000000ull;       // bound of every wait
-// Shared memory: raw slots first (1024-byte aligned for the 128-byte swizzle), then the B and A
-// halves of the operand slots (modulus 0 then modulus 1), then the mbarriers.
+// Shared memory: raw slots first (1024-byte aligned for the 128-byte swizzle), then the B halves
+// of the operand slots (column tile 0 then 1), the A halves, then the mbarriers.
 constexpr int OFF_B = RS * RAW_STAGE;
 constexpr int OFF_A = OFF_B + S * 2 * B_STAGE;
-constexpr int SMEM_RING = OFF_A + S * 2 * A_STAGE;
+constexpr int SMEM_RING = OFF_A + S * A_STAGE;
 constexpr int SMEM_BYTES = SMEM_RING + 2048;      // + barriers + slack to align the base to 1024
 static_assert(SMEM_BYTES <= 227 * 1024, "shared memory budget");
 static_assert(OFF_B % 1024 == 0 && OFF_A % 1024 == 0, "stage alignment");
-static_assert(NWC == 2 * S && RS == 2 * S, "slot ownership");
+constexpr int WPS = NWC / S;                      // converter warps per operand slot
+constexpr int ROWS_W = BM / WPS;                  // rows of a slab converted by one warp
+constexpr int COLS_W = 2 * BN / (NWC / 4);        // accumulator columns reduced by one warp
+static_assert(NWC % S == 0 && ROWS_W % 16 == 0 && RS == 2 * S, "slot ownership");
+static_assert(NWC % 4 == 0 && COLS_W % 32 == 0 && BN % COLS_W == 0, "accumulator split");
 constexpr uint64_t NCHUNK = 512;
 
 struct TcMod {
@@ -78,8 +85,9 @@ struct TcArgs {
     icm::ChunkTab tab;
     uint8_t *R;                       // [L][r][nch][sum M_c]
     uint64_t N, K, n0, nch;
-    uint32_t n_ntile, n_mod, n_pair;  // moduli 2 j and 2 j + 1 form pair j (the last may be single)
-    uint64_t n_tiles;
+    uint32_t n_mod;
+    uint32_t two;                     // the round has a second 256-column tile (nch > 256)
+    uint64_t n_tiles;                 // L x row tiles x moduli
     TcMod md[ICM_MAX_MODULI];
 };
 
@@ -220,16 +228,13 @@ struct __align__(8) Bars {
 static_assert(sizeof(Bars) <= 1024, "barrier block");
 
 struct TileCoord {
-    uint32_t l, c, mi, nt;            // mi: first modulus of the pair
-    bool two;                         // the pair holds a second modulus mi + 1
+    uint32_t l, c, mi;                // limb, chunk, modulus
     uint64_t m0, M;
 };
 __device__ __forceinline__ TileCoord tile_coord(const TcArgs &p, uint64_t tile) {
     TileCoord t;
     uint64_t tt = tile;
-    t.nt = (uint32_t)(tt % p.n_ntile); tt /= p.n_ntile;
-    t.mi = 2 * (uint32_t)(tt % p.n_pair); tt /= p.n_pair;
-    t.two = t.mi + 1 < p.n_mod;
+    t.mi = (uint32_t)(tt % p.n_mod); tt /= p.n_mod;
     const uint32_t mt_total = p.tab.mt0[p.tab.n];
     const uint32_t mtg = (uint32_t)(tt % mt_total);
     t.l = (uint32_t)(tt / mt_total);
@@ -241,9 +246,9 @@ __device__ __forceinline__ TileCoord tile_coord(const TcArgs &p, uint64_t tile) 
     return t;
 }
 
-// Converter warps w and w + 4 convert slab g (g mod 4 = w) together, 64 rows each, using operand
-// slot w and raw slot g mod 8; each warp meets its slots' phases in order.  The MMA thread issues
-// one MMA per modulus and slab.
+// Converter warps w, w + 4, w + 8 and w + 12 convert slab g (g mod 4 = w) together, 32 rows each,
+// using operand slot w and raw slot g mod 8; each warp meets its slots' phases in order.  The MMA
+// thread issues one MMA per modulus and slab.
 __global__ void __launch_bounds__(NWC * 32 + 96, 1) k_crt_tc(const __grid_constant__ TcArgs p) {
     constexpr int W_MMA = NWC, W_RAW = NWC + 1, W_QRY = NWC + 2;
     // a warp performs the reduction after flush point f before it converts a slab past f + LAG;
@@ -260,9 +265,9 @@ __global__ void __launch_bounds__(NWC * 32 + 96, 1) k_crt_tc(const __grid_consta
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     if (tid == 0) {
-        for (int s = 0; s < RS; ++s) { mbar_init(&bars->rawfull[s], 1); mbar_init(&bars->rawempty[s], 2); }
+        for (int s = 0; s < RS; ++s) { mbar_init(&bars->rawfull[s], 1); mbar_init(&bars->rawempty[s], WPS); }
         for (int s = 0; s < S; ++s) {
-            mbar_init(&bars->full[s], 2);
+            mbar_init(&bars->full[s], WPS);
             mbar_init(&bars->bfull[s], 1);
             mbar_init(&bars->empty[s], 1);
         }
@@ -289,27 +294,28 @@ __global__ void __launch_bounds__(NWC * 32 + 96, 1) k_crt_tc(const __grid_consta
     if (warp < W_MMA) {
         // ------------------------------------------------------------------ converter warps
         uint32_t acc_uses = 0;                   // acc_full completions consumed
-        const uint32_t qtr = warp & 3, hacc = warp >> 2;                 // TMEM lane quarter, accumulator
-        const uint32_t slot = warp & 3, half = warp >> 2;                // operand slot, row half
+        // TMEM lane quarter (a warp reaches lanes 32 (warp mod 4) ..), first accumulator column of
+        // this warp's share and the accumulator (modulus of the pair) it lies in
+        const uint32_t qtr = warp & 3, ccol = (uint32_t)(warp >> 2) * COLS_W, hacc = ccol / BN;
+        const uint32_t slot = warp % S, sub = warp / S;                  // operand slot, row block
         const uint32_t trow = qtr * 32 + lane;                           // accumulator row of this thread
-        // conversion map, item it = 0..3: row half*64 + it*16 + lrow, 16-byte chunks [4 cj, 4 cj + 4)
+        // conversion map, item it: row sub*ROWS_W + it*16 + lrow, 16-byte chunks [4 cj, 4 cj + 4)
         // of the swizzled 128-byte raw row -> 16 bytes of residues per modulus; every quarter-warp
         // covers 8 consecutive rows with the same chunks (8 distinct bank groups)
-        const uint32_t lrow = half * 64 + ((uint32_t)(lane >> 4) << 3) + (lane & 7);
+        const uint32_t lrow = sub * ROWS_W + ((uint32_t)(lane >> 4) << 3) + (lane & 7);
         const uint32_t cj = (lane >> 3) & 1;
         const uint32_t rsw = lane & 7;                                   // = row mod 8 for every item
         const uint32_t a_off = (cj * 16 + (lrow >> 3)) * 128 + (lrow & 7) * 16;
-        unsigned char *a_slot = sA + slot * 2 * A_STAGE + a_off;
+        unsigned char *a_slot = sA + slot * A_STAGE + a_off;
         uint64_t g0 = 0;                         // global index of the tile's first slab
         // every loop decision below is warp-uniform (__all_sync), because drain() issues
         // warp-collective TMEM instructions
         auto go = [&]() { return __all_sync(0xffffffffu, *abort_flag == 0); };
         for (uint64_t tile = blockIdx.x; tile < p.n_tiles && go(); tile += gridDim.x) {
             const TileCoord tc = tile_coord(p, tile);
-            const TcMod m0 = p.md[tc.mi], m1 = p.md[tc.two ? tc.mi + 1 : tc.mi];
-            const TcMod md = hacc ? m1 : m0;                             // modulus of this warp's accumulator
-            const bool mine = hacc == 0 || tc.two;                       // this warp's accumulator is in use
-            const uint64_t nb = (uint64_t)tc.nt * BN;
+            const TcMod md = p.md[tc.mi];
+            const bool mine = hacc == 0 || p.two;                        // this warp's accumulator is in use
+            const uint64_t nb = (uint64_t)hacc * BN;                     // first column of that accumulator
             const float fm = (float)md.m;
 
             // the reduction (or final write) of this warp's part of the accumulators
@@ -322,9 +328,9 @@ __global__ void __launch_bounds__(NWC * 32 + 96, 1) k_crt_tc(const __grid_consta
                 ++acc_uses;
                 tc_fence_after();
                 if (mine) {
-                    for (int rnd = 0; rnd < 8; ++rnd) {
-                        const uint32_t col0 = rnd * 32;
-                        const uint32_t taddr = tmem + ((qtr * 32) << 16) + hacc * 256 + col0;
+                    for (int rnd = 0; rnd < COLS_W / 32; ++rnd) {
+                        const uint32_t col0 = ccol % BN + rnd * 32;               // column within the accumulator
+                        const uint32_t taddr = tmem + ((qtr * 32) << 16) + hacc * BN + col0;
                         uint32_t v[32];
                         tmem_ld32(taddr, v);
                         if (!final) {
@@ -339,8 +345,7 @@ __global__ void __launch_bounds__(NWC * 32 + 96, 1) k_crt_tc(const __grid_consta
                             tmem_st32(taddr, v);
                         } else {
                             const uint64_t row = tc.m0 + trow;
-                            const uint32_t mi = tc.mi + hacc;
-                            uint8_t *Rl = p.R + ((size_t)tc.l * p.n_mod + mi) * p.nch * Mall + p.tab.row0[tc.c];
+                            uint8_t *Rl = p.R + ((size_t)tc.l * p.n_mod + tc.mi) * p.nch * Mall + p.tab.row0[tc.c];
 #pragma unroll
                             for (int j = 0; j < 32; ++j) {
                                 const uint64_t col = nb + col0 + j;
@@ -378,17 +383,15 @@ __global__ void __launch_bounds__(NWC * 32 + 96, 1) k_crt_tc(const __grid_consta
                 }
                 const unsigned char *r_base = sR + rslot * RAW_STAGE + lrow * 128;
 #pragma unroll
-                for (int it = 0; it < 4; ++it) {
+                for (int it = 0; it < ROWS_W / 16; ++it) {
                     const unsigned char *r_s = r_base + it * 16 * 128;
-                    uint32_t w0[4], w1[4];
+                    uint32_t w0[4];
 #pragma unroll
                     for (int h = 0; h < 4; ++h) {
                         const ulonglong2 zz = *reinterpret_cast<const ulonglong2 *>(r_s + (((cj * 4 + h) ^ rsw) << 4));
-                        w0[h] = res_pair(zz.x, zz.y, m0.wlo, m0.whi, m0.cbias, m0.magic, (uint32_t)m0.m, m0.hneg2);
-                        w1[h] = res_pair(zz.x, zz.y, m1.wlo, m1.whi, m1.cbias, m1.magic, (uint32_t)m1.m, m1.hneg2);
+                        w0[h] = res_pair(zz.x, zz.y, md.wlo, md.whi, md.cbias, md.magic, (uint32_t)md.m, md.hneg2);
                     }
                     *reinterpret_cast<uint4 *>(a_slot + it * 2 * 128) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
-                    *reinterpret_cast<uint4 *>(a_slot + A_STAGE + it * 2 * 128) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 // the warp barrier orders every lane's raw reads and residue writes before lane 0's
@@ -411,11 +414,11 @@ __global__ void __launch_bounds__(NWC * 32 + 96, 1) k_crt_tc(const __grid_consta
         uint32_t s = 0, u = 0;
         uint32_t acc_commits = 0;
         bool wait_free = false;
-        // descriptors of slot 0, modulus 0; slot s, modulus j adds (2 s + j) stage / 16 to the
-        // start-address field
+        // descriptors of slot 0 (column tile 0); slot s adds s A_STAGE / 16 to A's start-address
+        // field, and column tile j of slot s adds (2 s + j) B_STAGE / 16 to B's
         const uint64_t adesc0 = sdesc(smem_u32(sA), 2048, 128, 0), bdesc0 = sdesc(smem_u32(sB), 4096, 128, 0);
+        const bool two = p.two != 0;
         for (uint64_t tile = blockIdx.x; tile < p.n_tiles && !*abort_flag; tile += gridDim.x) {
-            const bool two = tile_coord(p, tile).two;
             bool alive = true;
             uint32_t to_flush = FLUSH_SLABS;                             // slabs to the next reduction
             for (uint64_t kt = 0; kt < nk; ++kt) {
@@ -429,10 +432,9 @@ __global__ void __launch_bounds__(NWC * 32 + 96, 1) k_crt_tc(const __grid_consta
                 }
                 tc_fence_after();
                 const uint32_t acc = kt > 0 ? 1u : 0u;
-                umma(tmem, adesc0 + (uint64_t)(2 * s * (A_STAGE >> 4)), bdesc0 + (uint64_t)(2 * s * (B_STAGE >> 4)), acc);
-                if (two)
-                    umma(tmem + 256, adesc0 + (uint64_t)((2 * s + 1) * (A_STAGE >> 4)),
-                         bdesc0 + (uint64_t)((2 * s + 1) * (B_STAGE >> 4)), acc);
+                const uint64_t ad = adesc0 + (uint64_t)(s * (A_STAGE >> 4));
+                umma(tmem, ad, bdesc0 + (uint64_t)(2 * s * (B_STAGE >> 4)), acc);
+                if (two) umma(tmem + BN, ad, bdesc0 + (uint64_t)((2 * s + 1) * (B_STAGE >> 4)), acc);
                 umma_commit(&bars->empty[s]);
                 if (++s == S) { s = 0; ++u; }
                 if (--to_flush == 0 || kt + 1 == nk) {                   // a reduction point
@@ -473,16 +475,17 @@ __global__ void __launch_bounds__(NWC * 32 + 96, 1) k_crt_tc(const __grid_consta
         uint64_t issued = 0;
         for (uint64_t tile = blockIdx.x; tile < p.n_tiles && !*abort_flag; tile += gridDim.x) {
             const TileCoord tc = tile_coord(p, tile);
-            // first block of this (limb, modulus, 256-column tile); the next modulus is one plane on
-            const unsigned char *b_src = p.Bt + ((size_t)tc.l * p.n_mod + tc.mi) * p.plane +
-                                         (size_t)((p.n0 + (uint64_t)tc.nt * BN) / BN) * (p.Kp / KS) * B_STAGE;
+            // first block of this (limb, modulus) for the round's first 256-column tile; the second
+            // tile's blocks follow Kp / 16 blocks later
+            const size_t tstep = (size_t)(p.Kp / KS) * B_STAGE;
+            const unsigned char *b_src = p.Bt + ((size_t)tc.l * p.n_mod + tc.mi) * p.plane + (size_t)(p.n0 / BN) * tstep;
             bool alive = true;
             for (uint64_t kt = 0; kt < nk; ++kt) {
                 if (u > 0 && !mbar_wait(&bars->empty[s], (u - 1) & 1, abort_flag)) { alive = false; break; }
-                mbar_expect_tx(&bars->bfull[s], tc.two ? 2 * B_STAGE : B_STAGE);
+                mbar_expect_tx(&bars->bfull[s], p.two ? 2 * B_STAGE : B_STAGE);
                 unsigned char *b_s = sB + s * 2 * B_STAGE;
                 bulk_load(smem_u32(b_s), b_src + kt * B_STAGE, B_STAGE, &bars->bfull[s]);
-                if (tc.two) bulk_load(smem_u32(b_s + B_STAGE), b_src + p.plane + kt * B_STAGE, B_STAGE, &bars->bfull[s]);
+                if (p.two) bulk_load(smem_u32(b_s + B_STAGE), b_src + tstep + kt * B_STAGE, B_STAGE, &bars->bfull[s]);
                 ++issued;
                 if (++s == S) { s = 0; ++u; }
             }
@@ -573,14 +576,13 @@ cudaError_t launch_ppmm_crt_tc(const I8Consts &k, const ChunkTab &tab, const voi
     a.R = reinterpret_cast<uint8_t *>(scratch);
     a.N = N; a.K = K;
     a.n_mod = k.n_mod;
-    a.n_pair = (k.n_mod + 1) / 2;
     for (uint32_t i = 0; i < k.n_mod; ++i)
         a.md[i] = TcMod{k.mod[i], k.wlo[i], k.whi[i], k.cbias[i], k.magic[i], k.hneg2[i], k.inv_m[i]};
     for (uint64_t n0 = 0; n0 < N; n0 += NCHUNK) {
         const uint64_t nch = std::min<uint64_t>(NCHUNK, N - n0);
         a.n0 = n0; a.nch = nch;
-        a.n_ntile = (uint32_t)((nch + BN - 1) / BN);
-        a.n_tiles = (uint64_t)k.n_limbs * tab.mt0[tab.n] * a.n_pair * a.n_ntile;
+        a.two = nch > (uint64_t)BN ? 1u : 0u;
+        a.n_tiles = (uint64_t)k.n_limbs * tab.mt0[tab.n] * k.n_mod;
         const uint64_t grid = std::min<uint64_t>(a.n_tiles, (uint64_t)sms);
         if (grid == 0) continue;
         k_crt_tc<<<(unsigned)grid, NWC * 32 + 96, SMEM_BYTES, st>>>(a);
