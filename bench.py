@@ -398,7 +398,7 @@ def main():
     gemm_avg_s = statistics.mean(gemm_ms) / 1e3
     peaks = measured_peaks()
     f = C.FORMS[args.form]
-    tc = tune is not None and tune.get("chosen") == 1
+    tc = tune is not None and tune.get("chosen") in (1, 2, 3, 4)
     if args.form == "u64":
         ops = 4.0 * M * n_cols * K * L                     # IMAD.WIDE per launch (2 x 2 30-bit limb products)
         sm_max = peaks.get("sm_max_mhz", 2070.0)
@@ -427,7 +427,7 @@ def main():
             roof = {"bound": "tensor", "achieved": ops / gemm_avg_s / 1e12, "peak": peak / 1e12, "unit": "TOP/s",
                     "peak_source": "measured in this run: int8 mma.sync.m16n8k32 issue-bound probe (no tcgen05 int8 on sm_103a)"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = NCU_TRAFFIC.get((args.form, 1 if tc else 0))
+    roof["traffic"] = NCU_TRAFFIC.get((args.form, tune["chosen"] if tc else 0))
     roof["kernel"] = {"u64": "k_ppmm_u64", "i8_digits": "k_ppmm_i8<0>", "i8_crt": "k_crt_p1<int8> + k_crt_combine",
                       "f16_crt": f"k_crt_tc ({C.VARIANTS[tune['chosen']]}) + k_crt_combine" if tc
                       else "k_crt_p1<fp16> + k_crt_combine"

@@ -374,7 +374,8 @@ cudaError_t crt_set_attributes() {
 }
 
 uint64_t crt_scratch_bytes(uint32_t n_limbs, uint32_t n_mod, uint64_t N, uint64_t M) {
-    return (uint64_t)n_limbs * n_mod * std::min<uint64_t>(N, NCHUNK) * M;
+    static_assert(NCHUNK == 512, "crt_scratch_main_bytes assumes 512-column rounds");
+    return crt_scratch_main_bytes(n_limbs, n_mod, N, M) + CRT_PROGRESS_BYTES;
 }
 
 bool make_chunk_tab(const uint64_t *const *A, uint64_t *const *C, const uint64_t *M, uint32_t n, ChunkTab &t) {
@@ -410,7 +411,7 @@ cudaError_t launch_ppmm_crt_grouped(bool f16, int bn, const I8Consts &k, const C
     const uint64_t Mall = tab.row0[tab.n];
     if (Mall == 0 || N == 0) return cudaSuccess;
     if (f16 && crt_tc_variant(bn) && tab.a_digits && crt_tc_supported(K))
-        return launch_ppmm_crt_tc(k, tab, Bp, N, K, Kp, scratch, st);
+        return launch_ppmm_crt_tc(k, tab, Bp, N, K, Kp, scratch, bn, st);
     if (bn != 128) bn = 256;
     for (uint64_t n0 = 0; n0 < N; n0 += NCHUNK) {
         const uint64_t nch = std::min<uint64_t>(NCHUNK, N - n0);

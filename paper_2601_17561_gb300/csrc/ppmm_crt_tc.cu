@@ -48,7 +48,6 @@
 namespace {
 
 constexpr int BM = 128, BN = 256, KS = 16;
-constexpr int NWC = 16;                           // converter warps (four per operand slot)
 constexpr int S = 4;                              // operand slots (A residues + B planes of 2 column tiles)
 constexpr int RS = 8;                             // raw database slots
 constexpr int FLUSH_SLABS = 64;                   // 1024 columns of K between reductions
@@ -65,11 +64,11 @@ constexpr int SMEM_RING = OFF_A + S * A_STAGE;
 constexpr int SMEM_BYTES = SMEM_RING + 2048;      // + barriers + slack to align the base to 1024
 static_assert(SMEM_BYTES <= 227 * 1024, "shared memory budget");
 static_assert(OFF_B % 1024 == 0 && OFF_A % 1024 == 0, "stage alignment");
-constexpr int WPS = NWC / S;                      // converter warps per operand slot
-constexpr int ROWS_W = BM / WPS;                  // rows of a slab converted by one warp
-constexpr int COLS_W = 2 * BN / (NWC / 4);        // accumulator columns reduced by one warp
-static_assert(NWC % S == 0 && ROWS_W % 16 == 0 && RS == 2 * S, "slot ownership");
-static_assert(NWC % 4 == 0 && COLS_W % 32 == 0 && BN % COLS_W == 0, "accumulator split");
+static_assert(RS == 2 * S, "raw slots per operand slot");
+// Progress bound between blocks (kernel option): blocks publish how many windows of SYNC_W slabs
+// they have issued, and no block starts a window more than SYNC_LAG windows ahead of the slowest.
+constexpr int SYNC_W = 64, SYNC_LAG = 2;
+static_assert(icm::CRT_PROGRESS_BYTES >= 1024 * 4, "progress words for up to 1024 blocks");
 constexpr uint64_t NCHUNK = 512;
 
 struct TcMod {
@@ -88,6 +87,7 @@ struct TcArgs {
     uint32_t n_mod;
     uint32_t two;                     // the round has a second 256-column tile (nch > 256)
     uint64_t n_tiles;                 // L x row tiles x moduli
+    uint32_t *prog;                   // per-block progress words (progress bound), zeroed per launch
     TcMod md[ICM_MAX_MODULI];
 };
 
@@ -249,8 +249,20 @@ __device__ __forceinline__ TileCoord tile_coord(const TcArgs &p, uint64_t tile) 
 // Converter warps w, w + 4, w + 8 and w + 12 convert slab g (g mod 4 = w) together, 32 rows each,
 // using operand slot w and raw slot g mod 8; each warp meets its slots' phases in order.  The MMA
 // thread issues one MMA per modulus and slab.
+//
+// NWC: converter warps (16: four per scheduler, register-capped at 96; 8: two per scheduler).
+// SYNC: bound the drift between blocks (see SYNC_W); the blocks that share a database row tile,
+// and those that share a modulus's query planes, then read each slab from L2 within a few
+// windows of one another instead of re-reading it from HBM.  Needs every block resident (the
+// launch is cooperative).
+template <int NWC, bool SYNC>
 __global__ void __launch_bounds__(NWC * 32 + 96, 1) k_crt_tc(const __grid_constant__ TcArgs p) {
     constexpr int W_MMA = NWC, W_RAW = NWC + 1, W_QRY = NWC + 2;
+    constexpr int WPS = NWC / S;                  // converter warps per operand slot
+    constexpr int ROWS_W = BM / WPS;              // rows of a slab converted by one warp
+    constexpr int COLS_W = 2 * BN / (NWC / 4);    // accumulator columns reduced by one warp
+    static_assert(NWC % S == 0 && ROWS_W % 16 == 0, "slot ownership");
+    static_assert(NWC % 4 == 0 && COLS_W % 32 == 0 && BN % COLS_W == 0, "accumulator split");
     // a warp performs the reduction after flush point f before it converts a slab past f + LAG;
     // a slab y can be converted while the MMA is blocked at f when its slot is free (y - S <= f)
     constexpr int LAG = S - 1;
@@ -449,26 +461,59 @@ __global__ void __launch_bounds__(NWC * 32 + 96, 1) k_crt_tc(const __grid_consta
         // make sure every MMA issued by this thread has completed before TMEM is freed
         umma_commit(&bars->done);
         mbar_wait_drain(&bars->done, 0);
-    } else if (warp == W_RAW && lane == 0) {
+    } else if (warp == W_RAW) {
         // ------------------------------------------------------------------ raw database producer
+        // lane 0 issues the loads; the whole warp evaluates the progress bound
         uint32_t rs = 0, ur = 0;
         uint64_t issued = 0;
-        for (uint64_t tile = blockIdx.x; tile < p.n_tiles && !*abort_flag; tile += gridDim.x) {
+        const uint32_t wpt = (uint32_t)((nk + SYNC_W - 1) / SYNC_W);       // windows per tile
+        uint32_t it = 0;                                                 // tiles begun by this block
+        bool alive = true;
+        for (uint64_t tile = blockIdx.x; alive && tile < p.n_tiles && !*abort_flag; tile += gridDim.x, ++it) {
             const TileCoord tc = tile_coord(p, tile);
-            bool alive = true;
             for (uint64_t kt = 0; kt < nk; ++kt) {
-                if (ur > 0 && !mbar_wait(&bars->rawempty[rs], (ur - 1) & 1, abort_flag)) { alive = false; break; }
-                mbar_expect_tx(&bars->rawfull[rs], RAW_STAGE);
-                tma_load_3d(smem_u32(sR + rs * RAW_STAGE), &p.tmA[tc.c], (int)(kt * KS), (int)tc.m0, (int)tc.l,
-                            &bars->rawfull[rs]);
+                if (SYNC && kt % SYNC_W == 0) {
+                    const uint32_t gw = it * wpt + (uint32_t)(kt / SYNC_W);    // window about to start
+                    if (lane == 0 && gw > 0) *(volatile uint32_t *)&p.prog[blockIdx.x] = gw;
+                    if (gw > (uint32_t)SYNC_LAG) {
+                        const uint64_t t0 = gtime();
+                        for (;;) {
+                            uint32_t lo = 0xFFFFFFFFu;
+                            for (uint32_t b = lane; b < gridDim.x; b += 32)
+                                lo = min(lo, *(volatile const uint32_t *)&p.prog[b]);
+                            lo = __reduce_min_sync(0xffffffffu, lo);
+                            if (lo >= gw - (uint32_t)SYNC_LAG) break;
+                            if (__any_sync(0xffffffffu, *abort_flag != 0)) { alive = false; break; }
+                            if (gtime() - t0 > WAIT_NS) {
+                                if (lane == 0) { *abort_flag = 1; atomicExch(&g_status, (uint32_t)ICM_DEV_TIMEOUT); }
+                                alive = false;
+                                break;
+                            }
+                            __nanosleep(256);
+                        }
+                        if (!alive) break;
+                    }
+                }
+                bool ok = true;
+                if (lane == 0) {
+                    ok = ur == 0 || mbar_wait(&bars->rawempty[rs], (ur - 1) & 1, abort_flag);
+                    if (ok) {
+                        mbar_expect_tx(&bars->rawfull[rs], RAW_STAGE);
+                        tma_load_3d(smem_u32(sR + rs * RAW_STAGE), &p.tmA[tc.c], (int)(kt * KS), (int)tc.m0, (int)tc.l,
+                                    &bars->rawfull[rs]);
+                    }
+                }
+                if (!__shfl_sync(0xffffffffu, ok, 0)) { alive = false; break; }
                 ++issued;
                 if (++rs == RS) { rs = 0; ++ur; }
             }
-            if (!alive) break;
         }
+        // this block holds no one back any more
+        if (SYNC && lane == 0) *(volatile uint32_t *)&p.prog[blockIdx.x] = 0xFFFFFFFFu;
         // every load issued by this thread has landed before the block exits
-        for (uint64_t i = (issued > (uint64_t)RS ? issued - RS : 0); i < issued; ++i)
-            mbar_wait_drain(&bars->rawfull[i % RS], (uint32_t)((i / RS) & 1));
+        if (lane == 0)
+            for (uint64_t i = (issued > (uint64_t)RS ? issued - RS : 0); i < issued; ++i)
+                mbar_wait_drain(&bars->rawfull[i % RS], (uint32_t)((i / RS) & 1));
     } else if (warp == W_QRY && lane == 0) {
         // ------------------------------------------------------------------ query plane producer
         uint32_t s = 0, u = 0;
@@ -526,7 +571,11 @@ EncodeTiled encode_fn() {
 namespace icm {
 
 cudaError_t crt_tc_set_attributes() {
-    return cudaFuncSetAttribute(k_crt_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    cudaError_t e = cudaFuncSetAttribute(k_crt_tc<16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_crt_tc<16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_crt_tc<8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_crt_tc<8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    return e;
 }
 
 // The tcgen05 path needs an even K (tensor-map row strides are multiples of 16 bytes); the caller
@@ -544,10 +593,12 @@ uint32_t device_status(bool clear) {
 }
 
 cudaError_t launch_ppmm_crt_tc(const I8Consts &k, const ChunkTab &tab, const void *Bp, uint64_t N, uint64_t K,
-                               uint64_t Kp, void *scratch, cudaStream_t st) {
+                               uint64_t Kp, void *scratch, int variant, cudaStream_t st) {
     const uint64_t Mall = tab.row0[tab.n];
     if (Mall == 0 || N == 0) return cudaSuccess;
-    if (!crt_tc_supported(K) || Kp % KS) return cudaErrorInvalidValue;
+    if (!crt_tc_supported(K) || Kp % KS || !crt_tc_variant(variant)) return cudaErrorInvalidValue;
+    const int nwc = variant <= 2 ? 16 : 8;
+    const bool sync = variant == 2 || variant == 4;
     EncodeTiled enc = encode_fn();
     if (!enc) return cudaErrorNotSupported;
     int dev = 0, sms = 0;
@@ -574,6 +625,10 @@ cudaError_t launch_ppmm_crt_tc(const I8Consts &k, const ChunkTab &tab, const voi
     a.plane = crt_f16_ncols(N) * Kp * 2;
     a.tab = tab;
     a.R = reinterpret_cast<uint8_t *>(scratch);
+    // progress words after the residue scratch (crt_scratch_bytes reserves them)
+    a.prog = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(scratch) +
+                                          crt_scratch_main_bytes(k.n_limbs, k.n_mod, N, Mall));
+    if (sms > 1024) return cudaErrorInvalidValue;
     a.N = N; a.K = K;
     a.n_mod = k.n_mod;
     for (uint32_t i = 0; i < k.n_mod; ++i)
@@ -585,8 +640,27 @@ cudaError_t launch_ppmm_crt_tc(const I8Consts &k, const ChunkTab &tab, const voi
         a.n_tiles = (uint64_t)k.n_limbs * tab.mt0[tab.n] * k.n_mod;
         const uint64_t grid = std::min<uint64_t>(a.n_tiles, (uint64_t)sms);
         if (grid == 0) continue;
-        k_crt_tc<<<(unsigned)grid, NWC * 32 + 96, SMEM_BYTES, st>>>(a);
-        cudaError_t e = cudaGetLastError();
+        cudaError_t e;
+        if (sync) {
+            // every block must be resident at once: a cooperative launch fails instead of stalling
+            e = cudaMemsetAsync(a.prog, 0, grid * sizeof(uint32_t), st);
+            if (e != cudaSuccess) return e;
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeCooperative;
+            attr[0].val.cooperative = 1;
+            cfg.gridDim = dim3((unsigned)grid);
+            cfg.blockDim = dim3((unsigned)(nwc * 32 + 96));
+            cfg.dynamicSmemBytes = SMEM_BYTES;
+            cfg.stream = st;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            e = nwc == 16 ? cudaLaunchKernelEx(&cfg, k_crt_tc<16, true>, a) : cudaLaunchKernelEx(&cfg, k_crt_tc<8, true>, a);
+        } else {
+            if (nwc == 16) k_crt_tc<16, false><<<(unsigned)grid, 16 * 32 + 96, SMEM_BYTES, st>>>(a);
+            else k_crt_tc<8, false><<<(unsigned)grid, 8 * 32 + 96, SMEM_BYTES, st>>>(a);
+            e = cudaGetLastError();
+        }
         if (e != cudaSuccess) return e;
         e = launch_crt_combine(k, tab, scratch, N, n0, nch, st);
         if (e != cudaSuccess) return e;

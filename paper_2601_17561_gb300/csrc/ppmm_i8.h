@@ -51,16 +51,19 @@ bool make_chunk_tab(const uint64_t *const *A, uint64_t *const *C, const uint64_t
 cudaError_t launch_ppmm_crt_grouped(bool f16, int bn, const I8Consts &k, const ChunkTab &tab, const void *Bp, uint64_t N,
                                     uint64_t K, uint64_t Kp, void *scratch, cudaStream_t st);
 cudaError_t crt_set_attributes();
-// Kernel variants of the CRT product (the column tile of the mma.sync kernel, or the tcgen05
-// kernel for the fp16 form on the balanced-digit database).
+// Kernel variants of the CRT product: the column tile of the mma.sync kernel (128, 256), or the
+// tcgen05 kernel for the fp16 form on the balanced-digit database: 1 = 16 converter warps,
+// 2 = 16 converter warps with the progress bound between blocks, 3 = 8 converter warps,
+// 4 = 8 converter warps with the progress bound.
 #define ICM_CRT_TCGEN05 1
-inline bool crt_tc_variant(int v) { return v == ICM_CRT_TCGEN05; }
+#define ICM_CRT_TCGEN05_LAST 4
+inline bool crt_tc_variant(int v) { return v >= ICM_CRT_TCGEN05 && v <= ICM_CRT_TCGEN05_LAST; }
 cudaError_t launch_crt_combine(const I8Consts &k, const ChunkTab &tab, const void *scratch, uint64_t N, uint64_t n0,
                                uint64_t nch, cudaStream_t st);
 cudaError_t crt_tc_set_attributes();
 bool crt_tc_supported(uint64_t K);
 cudaError_t launch_ppmm_crt_tc(const I8Consts &k, const ChunkTab &tab, const void *Bp, uint64_t N, uint64_t K, uint64_t Kp,
-                               void *scratch, cudaStream_t st);
+                               void *scratch, int variant, cudaStream_t st);
 uint32_t device_status(bool clear);
 // Residue planes of the query operand in the CRT forms.
 //  int8: [L][r][N][Kp], K contiguous.
@@ -80,7 +83,13 @@ __host__ __device__ __forceinline__ uint64_t crt_f16_off(uint64_t j, uint64_t k,
     return ((j >> 8) * (Kp >> 4) + (k >> 4)) * 4096 + ((((k >> 3) & 1) * 32 + ((j & 255) >> 3)) * 8 + (j & 7)) * 8 +
            (k & 7);
 }
-// small-modulus CRT forms (int8 or fp16 operands): query residue planes, two-phase product
+// small-modulus CRT forms (int8 or fp16 operands): query residue planes, two-phase product.
+// Scratch: the residue bytes [L][r][min(N, 512)][M] (rounded up to 256 bytes), then
+// CRT_PROGRESS_BYTES of progress words for the tcgen05 kernel's progress bound.
+constexpr uint64_t CRT_PROGRESS_BYTES = 4096;
+inline uint64_t crt_scratch_main_bytes(uint32_t n_limbs, uint32_t n_mod, uint64_t N, uint64_t M) {
+    return ((uint64_t)n_limbs * n_mod * (N < 512 ? N : 512) * M + 255) / 256 * 256;
+}
 uint64_t crt_scratch_bytes(uint32_t n_limbs, uint32_t n_mod, uint64_t N, uint64_t M);
 cudaError_t launch_crt_planes(bool f16, const I8Consts &k, const uint64_t *op, void *planes, uint64_t N, uint64_t K,
                               uint64_t Kp, cudaStream_t st);

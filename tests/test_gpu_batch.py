@@ -72,7 +72,7 @@ def test_autotune_keeps_results(setup):
     eng, dbs = setup["eng"], setup["dbs"]
     q = eng.prepare(setup["ct"], 3, "f16_crt")
     best, ms = eng.autotune(dbs, q)
-    assert best in (128, 256, 1) and all(m > 0 for m in ms)
+    assert best in (128, 256, 1, 2, 3, 4) and all(m > 0 for m in ms)
     outs = eng.match_batch(dbs, q)
     torch.cuda.synchronize()
     for s, ref in zip(outs, setup["ref"]):
@@ -92,11 +92,12 @@ def test_small_batches(setup, n_eyes):
         assert np.array_equal(s.residues(), ref[:, : n_eyes * 31, :])
 
 
-def test_grouped_tcgen05_variant(setup):
-    """tcgen05 variant over uneven chunks (ragged row tiles, partial column tile)."""
+@pytest.mark.parametrize("variant", [1, 2, 3, 4])
+def test_grouped_tcgen05_variant(setup, variant):
+    """tcgen05 variants over uneven chunks (ragged row tiles, partial column tile)."""
     from paper_2601_17561_gb300 import icm as C
     eng, dbs = setup["eng"], setup["dbs"]
-    C.icm_ctx_set_variant(eng.ctx, 1)
+    C.icm_ctx_set_variant(eng.ctx, variant)
     try:
         q = eng.prepare(setup["ct"], 3, "f16_crt")
         outs = eng.match_batch(dbs, q)
@@ -104,5 +105,28 @@ def test_grouped_tcgen05_variant(setup):
         C.icm_device_status(True)
         for s, ref in zip(outs, setup["ref"]):
             assert np.array_equal(s.residues(), ref)
+    finally:
+        C.icm_ctx_set_variant(eng.ctx, 0)
+
+
+@pytest.mark.parametrize("variant", [2, 4])
+def test_graph_replay_progress_bound_variant(setup, variant):
+    """The tcgen05 variants with the progress bound (cooperative launch, progress words reset by a
+    memset node) captured in the plan's CUDA graph: two replays give the oracle's folded scores."""
+    from paper_2601_17561_gb300 import icm as C
+    eng, dbs = setup["eng"], setup["dbs"]
+    C.icm_ctx_set_variant(eng.ctx, variant)
+    try:
+        st = torch.cuda.Stream()
+        plan = eng.plan(dbs, 3, "f16_crt", setup["ct"], st)
+        P = O.Params(**O.TINY)
+        for _ in range(2):
+            plan.launch(st)
+            st.synchronize()
+            C.icm_device_status(True)
+            for i, d in enumerate(dbs):
+                ids = O.db_layout(d.n_real, P.ndb, P.rho)
+                assert np.array_equal(plan.folded_residues(i), O.fold(P, setup["ref"][i], ids, 3, d.n_real))
+        del plan
     finally:
         C.icm_ctx_set_variant(eng.ctx, 0)
