@@ -12,15 +12,18 @@
 // feeds 512 columns.  (Two moduli on 256 columns each read the raw slab as often but convert it
 // twice: the conversion, integer work on the CUDA cores, was what bounded that layout.)
 //
-// Block: 16 converter warps, 1 MMA warp, 2 TMA producer warps; K advances in slabs of 16.
+// Block: 16 or 8 converter warps, 2 MMA issuer warps, 2 TMA producer warps; K advances in slabs
+// of 16.
 //  * Raw producer: one TMA load per slab of the 128 x 16 balanced-digit storage words of the
 //    database rows (128-byte swizzle: the 16-byte chunk c of row r sits at chunk c ^ (r mod 8)),
 //    into a ring of RS raw slots ("rawfull" / "rawempty" mbarriers).
 //  * Query producer: per slab, one bulk copy per modulus of the query's 8 KB residue block (the
 //    planes are stored pre-tiled in the MMA's K-major core-matrix layout, so a 256 x 16 operand is
 //    one contiguous block: 64 requests of 128 bytes, where a row-by-row tensor load of 32-byte rows
-//    needs 256) for each of the two column tiles into the B half of a ring of S operand slots
-//    ("bfull"; released by the MMA through "empty").
+//    needs 256) for each of the two column tiles into the B half of a ring of S operand slots.  It
+//    arrives on the slot's "full" mbarrier with the expected byte count, so "full" completes when
+//    the converters have written the A half and the B bytes have landed; the MMA issuers release
+//    the slot through "empty".
 //  * Converters: warps w, w + 4, w + 8 and w + 12 own operand slot w and raw slots w and w + 4, and
 //    convert every slab g with g mod 4 = w, 32 rows each: 8 consecutive storage words of a row become 8 fp16
 //    residues (two dp4a and a multiply-high division per residue, an f16x2 add per pair; no
@@ -28,8 +31,10 @@
 //    x 16-byte core matrices).  Every quarter-warp reads 8 distinct bank groups of the swizzled
 //    raw slot and writes 128 contiguous bytes.  The conversion is latency-bound integer work, so
 //    four warps per scheduler (rather than two) keep the integer pipes fed.
-//  * MMA: one elected thread issues one tcgen05.mma (M = 128, N = 256, K = 16) per column tile and
-//    slab and commits to the slot's "empty" mbarrier.  Every 64 slabs and at the end of a tile it
+//  * MMA: two issuing threads in different warps, one per 256-column tile (their accumulators are
+//    independent), each issue one tcgen05.mma (M = 128, N = 256, K = 16) per slab and commit to
+//    the slot's "empty" mbarrier (count 2).  Splitting the issue halves the per-slab control work
+//    on each thread, which bounded the single-issuer loop.  Every 64 slabs and at the end of a tile it
 //    commits to "acc_full"; the converters (warp w serves TMEM lane quarter w mod 4 and columns
 //    128 floor(w / 4) .. + 127 of the 512 accumulator columns) reduce the accumulators in place
 //    (tcgen05.ld / st) or write the final residues, and arrive on "acc_free".
@@ -221,7 +226,7 @@ __device__ __forceinline__ uint32_t res_pair(uint64_t z0, uint64_t z1, int wlo, 
 }
 
 struct __align__(8) Bars {
-    uint64_t rawfull[RS], rawempty[RS], full[S], bfull[S], empty[S], acc_full, acc_free, done;
+    uint64_t rawfull[RS], rawempty[RS], full[S], empty[S], acc_full, acc_free, done;
     uint32_t tmem;
     int abort_flag;
 };
@@ -256,8 +261,10 @@ __device__ __forceinline__ TileCoord tile_coord(const TcArgs &p, uint64_t tile) 
 // windows of one another instead of re-reading it from HBM.  Needs every block resident (the
 // launch is cooperative).
 template <int NWC, bool SYNC>
-__global__ void __launch_bounds__(NWC * 32 + 96, 1) k_crt_tc(const __grid_constant__ TcArgs p) {
-    constexpr int W_MMA = NWC, W_RAW = NWC + 1, W_QRY = NWC + 2;
+__global__ void __launch_bounds__(NWC * 32 + 128, 1) k_crt_tc(const __grid_constant__ TcArgs p) {
+    // warps: converters 0 .. NWC-1, MMA issuer of column tile 0, raw producer, query producer,
+    // MMA issuer of column tile 1
+    constexpr int W_MMA = NWC, W_RAW = NWC + 1, W_QRY = NWC + 2, W_MMA1 = NWC + 3;
     constexpr int WPS = NWC / S;                  // converter warps per operand slot
     constexpr int ROWS_W = BM / WPS;              // rows of a slab converted by one warp
     constexpr int COLS_W = 2 * BN / (NWC / 4);    // accumulator columns reduced by one warp
@@ -279,13 +286,12 @@ __global__ void __launch_bounds__(NWC * 32 + 96, 1) k_crt_tc(const __grid_consta
     if (tid == 0) {
         for (int s = 0; s < RS; ++s) { mbar_init(&bars->rawfull[s], 1); mbar_init(&bars->rawempty[s], WPS); }
         for (int s = 0; s < S; ++s) {
-            mbar_init(&bars->full[s], WPS);
-            mbar_init(&bars->bfull[s], 1);
-            mbar_init(&bars->empty[s], 1);
+            mbar_init(&bars->full[s], WPS + 1);
+            mbar_init(&bars->empty[s], 2);
         }
-        mbar_init(&bars->acc_full, 1);
+        mbar_init(&bars->acc_full, 2);
         mbar_init(&bars->acc_free, NWC);
-        mbar_init(&bars->done, 1);
+        mbar_init(&bars->done, 2);
         bars->abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -421,15 +427,19 @@ __global__ void __launch_bounds__(NWC * 32 + 96, 1) k_crt_tc(const __grid_consta
             if (go()) drain(true);
             g0 += nk;
         }
-    } else if (warp == W_MMA && lane == 0) {
-        // ------------------------------------------------------------------ MMA (one thread)
+    } else if ((warp == W_MMA || warp == W_MMA1) && lane == 0) {
+        // ------------------------------------------------------------------ MMA issuers (one thread each)
+        const uint32_t j = warp == W_MMA ? 0u : 1u;                      // column tile of this issuer
         uint32_t s = 0, u = 0;
         uint32_t acc_commits = 0;
         bool wait_free = false;
         // descriptors of slot 0 (column tile 0); slot s adds s A_STAGE / 16 to A's start-address
         // field, and column tile j of slot s adds (2 s + j) B_STAGE / 16 to B's
         const uint64_t adesc0 = sdesc(smem_u32(sA), 2048, 128, 0), bdesc0 = sdesc(smem_u32(sB), 4096, 128, 0);
-        const bool two = p.two != 0;
+        // without a second column tile the second issuer only takes part in the slot and
+        // reduction handshakes (its commits arrive at once)
+        const bool issue = j == 0 || p.two != 0;
+        const uint32_t dcol = j * BN;
         for (uint64_t tile = blockIdx.x; tile < p.n_tiles && !*abort_flag; tile += gridDim.x) {
             bool alive = true;
             uint32_t to_flush = FLUSH_SLABS;                             // slabs to the next reduction
@@ -438,15 +448,14 @@ __global__ void __launch_bounds__(NWC * 32 + 96, 1) k_crt_tc(const __grid_consta
                     if (!mbar_wait(&bars->acc_free, (acc_commits - 1) & 1, abort_flag)) { alive = false; break; }
                     wait_free = false;
                 }
-                if (!mbar_wait(&bars->full[s], u & 1, abort_flag) || !mbar_wait(&bars->bfull[s], u & 1, abort_flag)) {
+                if (!mbar_wait(&bars->full[s], u & 1, abort_flag)) {
                     alive = false;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t acc = kt > 0 ? 1u : 0u;
-                const uint64_t ad = adesc0 + (uint64_t)(s * (A_STAGE >> 4));
-                umma(tmem, ad, bdesc0 + (uint64_t)(2 * s * (B_STAGE >> 4)), acc);
-                if (two) umma(tmem + BN, ad, bdesc0 + (uint64_t)((2 * s + 1) * (B_STAGE >> 4)), acc);
+                if (issue)
+                    umma(tmem + dcol, adesc0 + (uint64_t)(s * (A_STAGE >> 4)),
+                         bdesc0 + (uint64_t)((2 * s + j) * (B_STAGE >> 4)), kt > 0 ? 1u : 0u);
                 umma_commit(&bars->empty[s]);
                 if (++s == S) { s = 0; ++u; }
                 if (--to_flush == 0 || kt + 1 == nk) {                   // a reduction point
@@ -527,17 +536,19 @@ __global__ void __launch_bounds__(NWC * 32 + 96, 1) k_crt_tc(const __grid_consta
             bool alive = true;
             for (uint64_t kt = 0; kt < nk; ++kt) {
                 if (u > 0 && !mbar_wait(&bars->empty[s], (u - 1) & 1, abort_flag)) { alive = false; break; }
-                mbar_expect_tx(&bars->bfull[s], p.two ? 2 * B_STAGE : B_STAGE);
+                mbar_expect_tx(&bars->full[s], p.two ? 2 * B_STAGE : B_STAGE);
                 unsigned char *b_s = sB + s * 2 * B_STAGE;
-                bulk_load(smem_u32(b_s), b_src + kt * B_STAGE, B_STAGE, &bars->bfull[s]);
-                if (p.two) bulk_load(smem_u32(b_s + B_STAGE), b_src + tstep + kt * B_STAGE, B_STAGE, &bars->bfull[s]);
+                bulk_load(smem_u32(b_s), b_src + kt * B_STAGE, B_STAGE, &bars->full[s]);
+                if (p.two) bulk_load(smem_u32(b_s + B_STAGE), b_src + tstep + kt * B_STAGE, B_STAGE, &bars->full[s]);
                 ++issued;
                 if (++s == S) { s = 0; ++u; }
             }
             if (!alive) break;
         }
+        // every load issued by this thread has landed before the block exits ("full" also needs
+        // the converters' arrivals, which a normal run always makes)
         for (uint64_t i = (issued > (uint64_t)S ? issued - S : 0); i < issued; ++i)
-            mbar_wait_drain(&bars->bfull[i % S], (uint32_t)((i / S) & 1));
+            mbar_wait_drain(&bars->full[i % S], (uint32_t)((i / S) & 1));
     }
     tc_fence_before();
     __syncthreads();
@@ -650,15 +661,15 @@ cudaError_t launch_ppmm_crt_tc(const I8Consts &k, const ChunkTab &tab, const voi
             attr[0].id = cudaLaunchAttributeCooperative;
             attr[0].val.cooperative = 1;
             cfg.gridDim = dim3((unsigned)grid);
-            cfg.blockDim = dim3((unsigned)(nwc * 32 + 96));
+            cfg.blockDim = dim3((unsigned)(nwc * 32 + 128));
             cfg.dynamicSmemBytes = SMEM_BYTES;
             cfg.stream = st;
             cfg.attrs = attr;
             cfg.numAttrs = 1;
             e = nwc == 16 ? cudaLaunchKernelEx(&cfg, k_crt_tc<16, true>, a) : cudaLaunchKernelEx(&cfg, k_crt_tc<8, true>, a);
         } else {
-            if (nwc == 16) k_crt_tc<16, false><<<(unsigned)grid, 16 * 32 + 96, SMEM_BYTES, st>>>(a);
-            else k_crt_tc<8, false><<<(unsigned)grid, 8 * 32 + 96, SMEM_BYTES, st>>>(a);
+            if (nwc == 16) k_crt_tc<16, false><<<(unsigned)grid, 16 * 32 + 128, SMEM_BYTES, st>>>(a);
+            else k_crt_tc<8, false><<<(unsigned)grid, 8 * 32 + 128, SMEM_BYTES, st>>>(a);
             e = cudaGetLastError();
         }
         if (e != cudaSuccess) return e;
