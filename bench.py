@@ -34,9 +34,11 @@ N_EYES, N_DB = 32, 7 * (1 << 14)
 WORKLOAD = ("paper-shaped CCMM + fold: 32 eyes x 31 rotations vs 114,688 codes (7 blocks of N_db=2^14), "
             "N_q=2^13, d=2^14, K=24,576, 8 primes < 2^60 (L_q=2), Delta=2^60")
 DTYPE = {"u64": "u64", "i8_digits": "int8", "i8_crt": "int8", "f16_crt": "f16"}
-# DRAM bytes per launch of the dominant kernel, keyed by (form, tcgen05 variant), from the
-# committed ncu captures (profiles/); None until a capture of the current kernel exists.
-NCU_TRAFFIC = {}
+# DRAM bytes (read + write) of the dominant kernel per CCMM call -- both column-round launches of
+# k_crt_tc, the unit `achieved` is timed on -- keyed by (form, tcgen05 variant), from the committed
+# one-pass ncu capture at this workload (profiles/k_crt_tc_paper_traffic.md); absent (null) for a
+# kernel changed since its capture.
+NCU_TRAFFIC = {("f16_crt", 3): 1.42e12 + 10.23e9 + 2.23e12 + 9.59e9}
 
 
 def _dist():
