@@ -38,7 +38,7 @@ DTYPE = {"u64": "u64", "i8_digits": "int8", "i8_crt": "int8", "f16_crt": "f16"}
 # k_crt_tc, the unit `achieved` is timed on -- keyed by (form, tcgen05 variant), from the committed
 # one-pass ncu capture at this workload (profiles/k_crt_tc_paper_traffic.md); absent (null) for a
 # kernel changed since its capture.
-NCU_TRAFFIC = {("f16_crt", 3): 1.42e12 + 10.23e9 + 2.23e12 + 9.59e9}
+NCU_TRAFFIC = {}
 
 
 def _dist():
@@ -400,7 +400,7 @@ def main():
     gemm_avg_s = statistics.mean(gemm_ms) / 1e3
     peaks = measured_peaks()
     f = C.FORMS[args.form]
-    tc = tune is not None and tune.get("chosen") in (1, 2, 3, 4, 5)
+    tc = tune is not None and tune.get("chosen") in (1, 2, 3, 4, 5, 6)
     if args.form == "u64":
         ops = 4.0 * M * n_cols * K * L                     # IMAD.WIDE per launch (2 x 2 30-bit limb products)
         sm_max = peaks.get("sm_max_mhz", 2070.0)

@@ -347,9 +347,8 @@ __global__ void __launch_bounds__(NWC * 32 + 128, 1) k_crt_tc(const __grid_const
     constexpr int W_MMA = NWC, W_RAW = NWC + 1, W_QRY = NWC + 2, W_MMA1 = NWC + 3;
     constexpr int WPS = NWC / S;                  // converter warps per operand slot
     constexpr int ROWS_W = BM / WPS;              // rows of a slab converted by one warp
-    constexpr int COLS_W = 2 * BN / (NWC / 4);    // accumulator columns reduced by one warp
     static_assert(NWC % S == 0 && ROWS_W % 16 == 0, "slot ownership");
-    static_assert(NWC % 4 == 0 && COLS_W % 32 == 0 && BN % COLS_W == 0, "accumulator split");
+    static_assert(NWC % 4 == 0 && NWC / 4 <= 16, "accumulator split over the lane quarters");
     // a warp performs the reduction after flush point f before it converts a slab past f + LAG;
     // a slab y can be converted while the MMA is blocked at f when its slot is free (y - S <= f)
     constexpr int LAG = S - 1;
@@ -406,9 +405,10 @@ __global__ void __launch_bounds__(NWC * 32 + 128, 1) k_crt_tc(const __grid_const
     if (warp < W_MMA) {
         // ------------------------------------------------------------------ converter warps
         uint32_t acc_uses = 0;                   // acc_full completions consumed
-        // TMEM lane quarter (a warp reaches lanes 32 (warp mod 4) ..), first accumulator column of
-        // this warp's share and the accumulator (modulus of the pair) it lies in
-        const uint32_t qtr = warp & 3, ccol = (uint32_t)(warp >> 2) * COLS_W, hacc = ccol / BN;
+        // TMEM lane quarter (a warp reaches lanes 32 (warp mod 4) ..) and this warp's share of the
+        // 16 32-column chunks of the two accumulators (the NWC / 4 warps of a quarter split them)
+        const uint32_t qtr = warp & 3, wq = (uint32_t)(warp >> 2);
+        const uint32_t c_lo = wq * 16 / (NWC / 4), c_hi = (wq + 1) * 16 / (NWC / 4);
         const uint32_t slot = warp % S, sub = warp / S;                  // operand slot, row block
         const uint32_t trow = qtr * 32 + lane;                           // accumulator row of this thread
         // conversion map, item it: row sub*ROWS_W + it*16 + lrow, 16-byte chunks [4 cj, 4 cj + 4)
@@ -426,8 +426,6 @@ __global__ void __launch_bounds__(NWC * 32 + 128, 1) k_crt_tc(const __grid_const
         for (uint64_t tile = t_first; tile < p.n_tiles && go(); tile += t_step) {
             const TileCoord tc = tile_coord<PAIR>(p, tile, rank);
             const TcMod md = p.md[tc.mi];
-            const bool mine = hacc == 0 || p.two;                        // this warp's accumulator is in use
-            const uint64_t nb = (uint64_t)hacc * BN;                     // first column of that accumulator
             const float fm = (float)md.m;
 
             // the reduction (or final write) of this warp's part of the accumulators
@@ -439,19 +437,20 @@ __global__ void __launch_bounds__(NWC * 32 + 128, 1) k_crt_tc(const __grid_const
                 }
                 ++acc_uses;
                 tc_fence_after();
-                if (mine) {
-                    // LDP loads of 32 columns in flight per wait (two when registers allow)
+                {
+                    // LDP loads of 32 columns in flight per wait (two when registers allow: 8
+                    // converter warps, 8 chunks each, pairs within one accumulator)
                     constexpr int LDP = NWC == 8 ? 2 : 1;
-                    for (int rnd = 0; rnd < COLS_W / 32; rnd += LDP) {
+                    for (uint32_t c = c_lo; c < c_hi; c += LDP) {
+                        if (c * 32 >= (uint32_t)BN && !p.two) break;        // the round has no second tile
                         uint32_t v[LDP][32];
 #pragma unroll
-                        for (int q = 0; q < LDP; ++q)
-                            tmem_ld32_nw(tmem + ((qtr * 32) << 16) + hacc * BN + ccol % BN + (rnd + q) * 32, v[q]);
+                        for (int q = 0; q < LDP; ++q) tmem_ld32_nw(tmem + ((qtr * 32) << 16) + (c + q) * 32, v[q]);
                         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
                         for (int q = 0; q < LDP; ++q) {
-                            const uint32_t col0 = ccol % BN + (rnd + q) * 32;         // column within the accumulator
-                            const uint32_t taddr = tmem + ((qtr * 32) << 16) + hacc * BN + col0;
+                            const uint32_t col0 = (c + q) * 32;                  // column of the round
+                            const uint32_t taddr = tmem + ((qtr * 32) << 16) + col0;
                             if (!final) {
                                 // x - m round(x / m): the fma adds 1.5 2^23 to the exact x / m
                                 // estimate and rounds once, which rounds it to an integer (|x / m| < 2^22)
@@ -467,7 +466,7 @@ __global__ void __launch_bounds__(NWC * 32 + 128, 1) k_crt_tc(const __grid_const
                                 uint8_t *Rl = p.R + ((size_t)tc.l * p.n_mod + tc.mi) * p.nch * Mall + p.tab.row0[tc.c];
 #pragma unroll
                                 for (int j = 0; j < 32; ++j) {
-                                    const uint64_t col = nb + col0 + j;
+                                    const uint64_t col = col0 + j;
                                     if (row < tc.M && col < p.nch && p.n0 + col < N) {
                                         int val = __float2int_rn(__uint_as_float(v[q][j])) % md.m;
                                         val = val < 0 ? val + md.m : val;
@@ -750,6 +749,7 @@ namespace icm {
 #define ICM_TC_V3 8, false, false, 4, 8
 #define ICM_TC_V4 8, true, false, 4, 8
 #define ICM_TC_V5 8, false, true, 4, 8
+#define ICM_TC_V6 12, false, false, 6, 6
 
 cudaError_t crt_tc_set_attributes() {
     const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
@@ -758,6 +758,7 @@ cudaError_t crt_tc_set_attributes() {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_crt_tc<ICM_TC_V3>, attr, Ring<4, 8>::SMEM);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_crt_tc<ICM_TC_V4>, attr, Ring<4, 8>::SMEM);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_crt_tc<ICM_TC_V5>, attr, Ring<4, 8>::SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_crt_tc<ICM_TC_V6>, attr, Ring<6, 6>::SMEM);
     return e;
 }
 
@@ -865,7 +866,8 @@ cudaError_t launch_ppmm_crt_tc(const I8Consts &k, const ChunkTab &tab, const voi
             cfg.gridDim = dim3((unsigned)(2 * n_cl));
             e = cudaLaunchKernelEx(&cfg, k_crt_tc<ICM_TC_V5>, a);
         } else {
-            if (nwc == 16) k_crt_tc<ICM_TC_V1><<<(unsigned)grid, 16 * 32 + 128, Ring<4, 8>::SMEM, st>>>(a);
+            if (variant == 6) k_crt_tc<ICM_TC_V6><<<(unsigned)grid, 12 * 32 + 128, Ring<6, 6>::SMEM, st>>>(a);
+            else if (nwc == 16) k_crt_tc<ICM_TC_V1><<<(unsigned)grid, 16 * 32 + 128, Ring<4, 8>::SMEM, st>>>(a);
             else k_crt_tc<ICM_TC_V3><<<(unsigned)grid, 8 * 32 + 128, Ring<4, 8>::SMEM, st>>>(a);
             e = cudaGetLastError();
         }
