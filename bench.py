@@ -38,7 +38,8 @@ DTYPE = {"u64": "u64", "i8_digits": "int8", "i8_crt": "int8", "f16_crt": "f16"}
 # k_crt_tc, the unit `achieved` is timed on -- keyed by (form, tcgen05 variant), from the committed
 # one-pass ncu capture at this workload (profiles/k_crt_tc_paper_traffic.md); absent (null) for a
 # kernel changed since its capture.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {("f16_crt", 3): 1.89e12 + 10.23e9 + 2.21e12 + 9.59e9,
+               ("f16_crt", 1): 1.53e12 + 10.23e9 + 2.41e12 + 9.59e9}
 
 
 def _dist():
