@@ -320,7 +320,7 @@ def main():
         return run_serving(args, dev)
     from paper_2601_17561_gb300 import engine as E
     from paper_2601_17561_gb300 import icm as C
-    from paper_2601_17561_gb300 import synth
+    from paper_2601_17561_gb300 import shard
 
     def barrier():
         if ws > 1:
@@ -328,10 +328,9 @@ def main():
         torch.cuda.synchronize()
 
     # ---- setup (untimed): resident encrypted database shard and the query ciphertext
-    W = synth.make_workload(n_eyes=N_EYES, n_db=N_DB, seed=2 + 1000 * rank, planted_frac=0.05)
-    Wq = synth.make_workload(n_eyes=N_EYES, n_db=0, seed=2) if rank else W
+    W, Wq = shard.shard_workload(rank, N_EYES, N_DB, seed=2)
     eng = E.Engine(**E.PAPER).keygen()
-    db = eng.encrypt_db(W.db_codes, W.db_masks, chunk_id=rank)
+    db = eng.encrypt_db(W.db_codes, W.db_masks, chunk_id=shard.chunk_id(rank))
     ct = eng.encrypt_query(Wq.q_codes, Wq.q_masks, Wq.eye_ids)
     torch.cuda.synchronize()
     st = torch.cuda.Stream(device=dev)
@@ -390,11 +389,8 @@ def main():
     total_ms, gemm_ms = timed_form(args.form, args.steps, max(args.warmup, 1))
     clk = clocks.stop()
     barrier()
-    t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_per_step = t.item() / args.steps
-    value = ws * comps / (ms_per_step / 1e3)
+    ms_per_step = shard.job_time_ms(total_ms, dist if ws > 1 else None, dev) / args.steps
+    value = shard.job_rate(ws, comps, ms_per_step)
 
     # ---- roofline of the dominant kernel (the CCMM product)
     M, K, L, n_cols = db.m_rows, eng.K, eng.L, N_EYES * 31
@@ -463,11 +459,9 @@ def main():
         b.record(st)
         st.synchronize()
     e2e_ms = a.elapsed_time(b) / args.e2e_steps
-    te = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-    if ws > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e = {"value": ws * comps / (te.item() / 1e3), "unit": UNIT, "h2d_bytes_per_step": ct_bytes,
-           "d2h_bytes_per_step": fo_bytes, "ms_per_step": te.item()}
+    te = shard.job_time_ms(e2e_ms, dist if ws > 1 else None, dev)
+    e2e = {"value": shard.job_rate(ws, comps, te), "unit": UNIT, "h2d_bytes_per_step": ct_bytes,
+           "d2h_bytes_per_step": fo_bytes, "ms_per_step": te}
     del wsbuf
 
     n_chunks = (N_EYES * 31 + 511) // 512

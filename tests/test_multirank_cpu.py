@@ -1,0 +1,81 @@
+"""The N > 1 path on CPU: two gloo ranks, each with its own encrypted database shard (own a-part
+stream) and the same query batch, computed with the oracle; no data moves between ranks except
+the test's own gathers.  The union of the ranks' decrypted scores must equal the cleartext inner
+products of the common queries against the union of the shards, and the job time is the maximum
+over ranks."""
+import os
+import socket
+
+import numpy as np
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+import oracle as O
+from paper_2601_17561_gb300 import shard
+
+CFG = dict(log_n_db=6, log_n_q=5, n_limbs=3, n_limbs_q=1, prime_bits=50, log2_delta=26, seed=11)
+N_EYES, N_DB, WORLD = 2, 40, 2
+
+
+def _free_port() -> int:
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out_q):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        P = O.Params(h=16, **CFG)
+        W, Wq = shard.shard_workload(rank, N_EYES, N_DB, seed=5)
+        ids = O.db_layout(N_DB, P.ndb, P.rho)
+        A = O.db_rows(P, W.db_codes, W.db_masks, ids, chunk=shard.chunk_id(rank))
+        B = O.query_extend(P, O.query_encrypt(P, Wq.q_codes, Wq.q_masks, Wq.eye_ids))
+        C = O.ppmm(P.q, A, B)
+        dec = np.zeros((C.shape[1], N_DB), np.int64)
+        for j in range(C.shape[1]):
+            b_ids, nums, _ = O.decrypt_column(P, C[:, j, :], ids)
+            real = b_ids < N_DB
+            dec[j, b_ids[real]] = nums[real]
+        queries = [None] * world
+        dist.all_gather_object(queries, (Wq.q_codes.tobytes(), Wq.q_masks.tobytes(), Wq.eye_ids.tobytes()))
+        shards = [None] * world
+        dist.all_gather_object(shards, (W.db_codes, W.db_masks, dec, A[:, : P.ndb, :8].copy()))
+        t = shard.job_time_ms(10.0 * (rank + 1), dist)
+        if rank == 0:
+            out_q.put((queries, shards, t, Wq.q_codes, Wq.q_masks))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_ranks_shard_the_database():
+    O.build()
+    ctx = mp.get_context("spawn")
+    out_q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, WORLD, port, out_q)) for r in range(WORLD)]
+    for p in procs:
+        p.start()
+    queries, shards, t, q_codes, q_masks = out_q.get(timeout=300)
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    # every rank matched the same query batch
+    assert all(q == queries[0] for q in queries)
+    # the shards differ, and so do their a-parts (chunk ids key the a-part streams)
+    assert not np.array_equal(shards[0][0], shards[1][0])
+    assert not np.array_equal(shards[0][3], shards[1][3])
+    # union of the ranks' decrypted scores == cleartext inner products against the union
+    P = O.Params(h=16, **CFG)
+    codes = np.concatenate([s[0] for s in shards])
+    masks = np.concatenate([s[1] for s in shards])
+    rc, rm = O.rotated_templates(q_codes, q_masks, P.rho)
+    num, den = O.hd_counts(rc, rm, O.unpack(codes), O.unpack(masks))
+    want = O.inner_from_counts(num, den)
+    got = np.concatenate([s[2] for s in shards], axis=1)
+    assert np.array_equal(got, want)
+    # the job time is the slowest rank's; the rate counts every rank's comparisons
+    assert t == 10.0 * WORLD
+    assert shard.job_rate(WORLD, N_EYES * N_DB, t) == WORLD * N_EYES * N_DB / (t / 1e3)
