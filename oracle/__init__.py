@@ -76,6 +76,8 @@ def lib():
         _lib.orc_hd_counts.argtypes = [i32, i32, i32, vp, vp, vp, vp, vp, vp]
         _lib.orc_negacyclic_mul.restype = None
         _lib.orc_negacyclic_mul.argtypes = [vp, vp, i32, u64, vp]
+        _lib.orc_rescale.restype = None
+        _lib.orc_rescale.argtypes = [i32, i32, vp, ctypes.c_size_t, vp, vp]
         _lib.orc_omp_threads.restype = i32
         _lib.orc_omp_threads.argtypes = []
     return _lib
@@ -452,6 +454,38 @@ def crt_decode(P: Params, D: np.ndarray) -> np.ndarray:
     return nums.reshape(D.shape[1:]), worst
 
 
+def rescale(P: Params, C: np.ndarray) -> np.ndarray:
+    """Rescaling by Q' (orc_rescale): residues C [L][...] modulo Q_db = Q Q' -> [L_q][...] modulo
+    Q, x' = round(x / Q') with the base-conversion correction decided in IEEE double."""
+    L, Lq = P.n_limbs, P.n_limbs_q
+    flat = np.ascontiguousarray(C.reshape(L, -1), np.uint64)
+    out = np.zeros((Lq, flat.shape[1]), np.uint64)
+    q = np.array(P.q, np.uint64)
+    lib().orc_rescale(L, Lq, _p(q), flat.shape[1], _p(flat), _p(out))
+    return out.reshape((Lq,) + C.shape[1:])
+
+
+def crt_decode_q(P: Params, D: np.ndarray) -> tuple:
+    """crt_decode at the rescaled level: residues D [L_q][...] modulo Q, centred, divided by Delta
+    and rounded (the scores after rescaling by Q' carry the scale Delta)."""
+    q = [int(v) for v in P.q[: P.n_limbs_q]]
+    Q = P.Q
+    scale = 1 << P.log2_delta
+    Lq = D.shape[0]
+    flat = D.reshape(Lq, -1)
+    coeffs = [(Q // qi) * pow(Q // qi, -1, qi) for qi in q]
+    nums = np.zeros(flat.shape[1], np.int64)
+    worst = 0.0
+    for c in range(flat.shape[1]):
+        x = sum(int(flat[l, c]) * coeffs[l] for l in range(Lq)) % Q
+        if x > Q // 2:
+            x -= Q
+        n = (2 * x + scale) // (2 * scale)
+        nums[c] = n
+        worst = max(worst, abs(x - n * scale) / scale)
+    return nums.reshape(D.shape[1:]), worst
+
+
 def decrypt_rows(P: Params, Ca: np.ndarray, Cb: np.ndarray, b_rows) -> np.ndarray:
     """Residues of Dec = Cb + S_db * Ca for the given logical b-rows of one result column."""
     b_rows = np.ascontiguousarray(np.asarray(b_rows, np.int64))
@@ -464,9 +498,10 @@ def decrypt_rows(P: Params, Ca: np.ndarray, Cb: np.ndarray, b_rows) -> np.ndarra
     return D
 
 
-def decrypt_column(P: Params, Ccol: np.ndarray, row_ids) -> tuple:
-    """Decrypt every b-row of one result column Ccol [L][M] (chunk row layout).  Returns
-    (logical b-row ids, numerators, worst relative error)."""
+def decrypt_column(P: Params, Ccol: np.ndarray, row_ids, rescaled: bool = False) -> tuple:
+    """Decrypt every b-row of one result column Ccol [L][M] (chunk row layout; [L_q][M] modulo Q
+    with scale Delta when `rescaled`).  Returns (logical b-row ids, numerators, worst relative
+    error)."""
     row_ids = np.asarray(row_ids, np.int64)
     a_pos = np.array([np.where(row_ids == i)[0][0] for i in range(P.ndb)])
     b_sel = np.where(row_ids >= P.ndb)[0]
@@ -474,5 +509,5 @@ def decrypt_column(P: Params, Ccol: np.ndarray, row_ids) -> tuple:
     Cb = Ccol[:, b_sel]
     b_ids = row_ids[b_sel] - P.ndb
     D = decrypt_rows(P, Ca, Cb, b_ids)
-    nums, worst = crt_decode(P, D)
+    nums, worst = crt_decode_q(P, D) if rescaled else crt_decode(P, D)
     return b_ids, nums, worst

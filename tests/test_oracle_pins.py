@@ -352,3 +352,74 @@ def test_ccmm_decrypts_to_cleartext_inner_products(P):
                         v = inner[e * P.rho + rr, gsrc]
                     want += sign * v
                 assert nums[x] == want
+
+
+# ----------------------------------------------------------------------------- rescaling
+
+@pytest.mark.parametrize("P", [SMALL, SMALL2])
+def test_rescale_is_rounded_division(P):
+    """Rescaling by Q' (Section 2.2.2, Maintenance) equals round(x / Q') mod Q computed with
+    Python integers, on random coefficients and on the closed-form cases k Q' + e (|e| < Q'/2,
+    which round to k) and the ends of [0, Q Q')."""
+    rng = np.random.default_rng(3)
+    Qdb, Qp, Q = P.Qdb, P.Qp, P.Q
+    xs = [int.from_bytes(rng.bytes(64), "little") % Qdb for _ in range(400)]
+    ks = [0, 1, 2, Q // 3, Q - 1]
+    es = [0, 1, -1, Qp // 2, -(Qp // 2), Qp // 3]
+    xs += [(k * Qp + e) % Qdb for k in ks for e in es] + [0, Qdb - 1, Qp // 2, Qp // 2 + 1]
+    C = np.array([[x % ql for x in xs] for ql in P.q], np.uint64)
+    got = O.rescale(P, C)
+    # exact nearest integer; within 2^-40 of a half-integer the double-precision correction may
+    # take either neighbour (x = floor(Q'/2) is such a case: x / Q' = 1/2 - 1/(2 Q'))
+    for idx, x in enumerate(xs):
+        want = (2 * x + Qp) // (2 * Qp)
+        near_tie = abs(2 * (x % Qp) - Qp) < (Qp >> 40)
+        cands = [want, want - 1, want + 1] if near_tie else [want]
+        res = [int(got[j, idx]) for j in range(P.n_limbs_q)]
+        assert any(res == [(c % Q) % qj for qj in P.q[: P.n_limbs_q]] for c in cands), (idx, x)
+        if not near_tie:
+            assert res == [(want % Q) % qj for qj in P.q[: P.n_limbs_q]]
+    assert any(abs(2 * (x % Qp) - Qp) < (Qp >> 40) for x in xs)        # the tie window is exercised
+    # the closed-form cases directly: k Q' + e rounds to k (|e| <= Q'/3, away from the ties)
+    for k in ks:
+        for e in es:
+            if abs(e) <= Qp // 3 and (k * Qp + e) % Qdb == k * Qp + e:
+                idx = xs.index((k * Qp + e) % Qdb)
+                assert [int(got[j, idx]) for j in range(P.n_limbs_q)] == [k % qj for qj in P.q[: P.n_limbs_q]]
+
+
+@pytest.mark.parametrize("P", [SMALL, SMALL2])
+def test_rescaled_ccmm_decrypts_exactly(P):
+    """Dec at modulus Q of the rescaled CCMM result, divided by Delta and rounded, gives the
+    cleartext inner products <c'_db, c'_q> exactly (the rescaling error, at most (1 + h) / 2 per
+    coefficient, stays far below Delta / 2), and rescaling commutes with the fold up to the same
+    error: both orders decrypt to the cleartext fold."""
+    n_db = 70
+    W = synth.make_workload(n_eyes=2, n_db=n_db, seed=8, planted_frac=0.1)
+    B = O.query_extend(P, O.query_encrypt(P, W.q_codes, W.q_masks, W.eye_ids))
+    ids = O.db_layout(n_db, P.ndb, P.rho)
+    C = O.ppmm(P.q, O.db_rows(P, W.db_codes, W.db_masks, ids), B)
+    R = O.rescale(P, C)
+    assert R.shape == (P.n_limbs_q,) + C.shape[1:]
+    rc, rm = O.rotated_templates(W.q_codes, W.q_masks, P.rho)
+    num, den = O.hd_counts(rc, rm, O.unpack(W.db_codes), O.unpack(W.db_masks))
+    inner = O.inner_from_counts(num, den)
+    dec = np.zeros((R.shape[1], n_db), np.int64)
+    for j in range(R.shape[1]):
+        b_ids, nums, worst = O.decrypt_column(P, R[:, j, :], ids, rescaled=True)
+        real = b_ids < n_db
+        dec[j, b_ids[real]] = nums[real]
+        assert worst < 1e-3
+    assert np.array_equal(dec, inner)
+    # fold then rescale, and rescale then fold (the fold is linear per limb): same decryption
+    F0 = O.fold(P, C, ids, n_eyes=2, n_real=n_db)
+    F1 = O.rescale(P, F0)
+    Pq = O.Params(**{**P.__dict__, "n_limbs": P.n_limbs_q})
+    F2 = O.fold(Pq, R, ids, n_eyes=2, n_real=n_db)
+    for col in range(F1.shape[1]):
+        b1, n1, _ = O.decrypt_column(P, F1[:, col, :], ids, rescaled=True)
+        b2, n2, _ = O.decrypt_column(P, F2[:, col, :], ids, rescaled=True)
+        _, n0, _ = O.decrypt_column(P, F0[:, col, :], ids)
+        real = b1 < n_db                      # the fold writes the tail rows of a partial block as zero
+        assert np.array_equal(b1, b2) and np.array_equal(n1[real], n2[real])
+        assert np.array_equal(n1[real], n0[real])
