@@ -433,6 +433,30 @@ def main():
                       }.get(args.form)
     roof["ms_per_launch"] = gemm_avg_s * 1e3
 
+    # ---- rescaling by Q' of the step's CCMM result (not part of the timed step): HBM-bound, reads
+    # L words and writes L_q words per coefficient
+    rs = None
+    if eng.L > eng.Lq:
+        with torch.cuda.stream(st):
+            q1 = eng.prepare(ct, N_EYES, C.FORMS[args.form], stream=st)
+            s1 = eng.match(db, q1, stream=st)
+            out = E._u8(C.icm_rescale_bytes(s1.handle), dev)
+            eng.rescale(s1, stream=st, out=out)                         # warm-up
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 5
+            a.record(st)
+            for _ in range(reps):
+                eng.rescale(s1, stream=st, out=out)
+            b.record(st)
+            st.synchronize()
+        rms = a.elapsed_time(b) / reps
+        rbytes = (L + eng.Lq) * n_cols * M * 8
+        rpeak = peaks.get("hbm_gbs", 6800.0)
+        rs = {"kernel": "k_rescale", "ms_per_launch": rms, "bytes": rbytes, "achieved_gbs": rbytes / (rms / 1e3) / 1e9,
+              "peak_gbs": rpeak, "frac": rbytes / (rms / 1e3) / 1e9 / rpeak,
+              "peak_source": "of measured: MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "of fallback: 6.8 TB/s"}
+        del q1, s1, out
+
     # ---- other forms, one timed step each on the same workload
     forms = {args.form: {"value": value, "ms_per_step": ms_per_step}}
     for other in [x for x in args.compare_forms.split(",") if x and x != args.form]:
@@ -474,7 +498,7 @@ def main():
                        "l2": "inputs larger than L2 (206 GB resident database), no flush",
                        "parallelism": "replicas" if ws == 1 else f"weak: {ws} database shards, same query"},
             "roofline": roof, "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clk,
-            "forms": forms, "variant": tune}
+            "forms": forms, "variant": tune, "rescale": rs}
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         v, thr, sample, _ = oracle_sample(seconds_target=15.0)

@@ -175,11 +175,24 @@ void icm_scores_destroy(icm_scores *s);
 /* Shape of a scores buffer: limbs, columns, rows. */
 icm_status icm_scores_shape(const icm_scores *s, size_t *n_limbs, size_t *n_cols, size_t *m_rows);
 
-/* Decrypt for checking only (Section 2.2.2 Dec = a*sk + b, then rounding by Q' * Delta): for
- * every column and every real database row, the integer numerator <c'_db, c'_q> (unfolded
- * scores) or the folded sum of numerators.  dev_num: int64 [n_cols][n_db].  Threshold
- * decryption is outside this library. */
+/* Decrypt for checking only (Section 2.2.2 Dec = a*sk + b, then rounding by Q' * Delta, or by
+ * Delta modulo Q for rescaled scores): for every column and every real database row, the integer
+ * numerator <c'_db, c'_q> (unfolded scores) or the folded sum of numerators.  dev_num: int64
+ * [n_cols][n_db].  Threshold decryption is outside this library. */
 icm_status icm_decrypt_scores(icm_ctx *ctx, const icm_scores *s, int64_t *dev_num, size_t n, void *stream);
+
+/* Rescaling by Q' (Section 2.2.2, Maintenance: RS divides a ciphertext by a modulus factor and
+ * rounds): scores at modulus Q_db = Q Q' (L limbs) become scores at the query modulus Q (the
+ * first L_q limbs) with scale Delta, x' = round(x / Q') mod Q for every coefficient of both
+ * ciphertext parts (base conversion from the limbs of Q' with the correction decided in IEEE
+ * double: a coefficient within rounding error of a half-integer may round to either neighbour,
+ * inside the rescaling error).  Works on folded or unfolded scores (the fold commutes with it up
+ * to that error) and cuts their size L / L_q times.  icm_rescale_bytes gives the size of
+ * dev_out (caller-owned, [L_q][n_cols][M] u64).  Errors: ICM_EINVAL (already rescaled, L_q = L,
+ * or a handle of another context), ICM_ENOMEM (dev_out too small), ICM_ECUDA. */
+icm_status icm_rescale_bytes(const icm_scores *in, size_t *bytes);
+icm_status icm_rescale(icm_ctx *ctx, const icm_scores *in, void *dev_out, size_t bytes, void *stream,
+                       icm_scores **out);
 
 /* ---------------------------------------------------------------- batching form ---- */
 

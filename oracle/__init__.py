@@ -456,7 +456,7 @@ def crt_decode(P: Params, D: np.ndarray) -> np.ndarray:
 
 def rescale(P: Params, C: np.ndarray) -> np.ndarray:
     """Rescaling by Q' (orc_rescale): residues C [L][...] modulo Q_db = Q Q' -> [L_q][...] modulo
-    Q, x' = round(x / Q') with the base-conversion correction decided in IEEE double."""
+    Q, x' = round(x / Q') with the base-conversion correction from a 64-bit fixed-point sum."""
     L, Lq = P.n_limbs, P.n_limbs_q
     flat = np.ascontiguousarray(C.reshape(L, -1), np.uint64)
     out = np.zeros((Lq, flat.shape[1]), np.uint64)

@@ -197,6 +197,36 @@ icm_status icm_ctx_create(const icm_params *p, icm_ctx **out) {
     long double qod = 1;
     for (uint32_t l = 0; l < P.n_limbs_q; ++l) qod *= (long double)q[l];
     c->crt.q_over_delta = (double)(qod / exp2l((long double)P.log2_delta));
+    // decoding at the rescaled level (modulus Q, L_q limbs; same Q / Delta) and the rescaling
+    c->crt_q = c->crt;
+    c->rs = icm::RescaleConsts{};
+    c->rs.L = P.n_limbs; c->rs.Lq = P.n_limbs_q;
+    for (uint32_t l = 0; l < P.n_limbs; ++l) c->rs.q[l] = q[l];
+    for (uint32_t l = 0; l < P.n_limbs_q; ++l) {
+        uint64_t hat = 1 % q[l];
+        for (uint32_t j = 0; j < P.n_limbs_q; ++j) if (j != l) hat = mulmod(hat, q[j] % q[l], q[l]);
+        c->crt_q.inv[l] = powmod(hat, q[l] - 2, q[l]);
+        c->crt_q.invs[l] = shoup_of(c->crt_q.inv[l], q[l]);
+    }
+    for (uint32_t i = P.n_limbs_q; i < P.n_limbs; ++i) {
+        uint64_t hat = 1 % q[i];
+        for (uint32_t k = P.n_limbs_q; k < P.n_limbs; ++k) if (k != i) hat = mulmod(hat, q[k] % q[i], q[i]);
+        c->rs.yinv[i] = powmod(hat, q[i] - 2, q[i]);
+        c->rs.yinvs[i] = shoup_of(c->rs.yinv[i], q[i]);
+        c->rs.rhi[i] = c->crt.rhi[i]; c->rs.rlo[i] = c->crt.rlo[i];
+    }
+    for (uint32_t j = 0; j < P.n_limbs_q; ++j) {
+        uint64_t qp = 1 % q[j];
+        for (uint32_t i = P.n_limbs_q; i < P.n_limbs; ++i) {
+            uint64_t hat = 1 % q[j];
+            for (uint32_t k = P.n_limbs_q; k < P.n_limbs; ++k) if (k != i) hat = mulmod(hat, q[k] % q[j], q[j]);
+            c->rs.w[j][i] = hat;
+            c->rs.ws[j][i] = shoup_of(hat, q[j]);
+            qp = mulmod(qp, q[i] % q[j], q[j]);
+        }
+        c->rs.qp[j] = qp; c->rs.qps[j] = shoup_of(qp, q[j]);
+        c->rs.qpinv[j] = powmod(qp, q[j] - 2, q[j]); c->rs.qpinvs[j] = shoup_of(c->rs.qpinv[j], q[j]);
+    }
     *out = c;
     return ICM_OK;
 }
@@ -442,13 +472,15 @@ icm_status icm_fold(icm_ctx *c, const icm_scores *in, void *dev_out, size_t byte
     if (in->ctx != c) return fail(ICM_EINVAL, "handle from another context");
     if (in->folded) return fail(ICM_EINVAL, "scores are already folded");
     const uint32_t groups = (c->p.rho + c->p.fold_k - 1) / c->p.fold_k;
-    const size_t need = (size_t)c->p.n_limbs * in->n_eyes * groups * in->lay.M * 8;
+    const uint32_t limbs = in->rescaled ? c->p.n_limbs_q : c->p.n_limbs;
+    const size_t need = (size_t)limbs * in->n_eyes * groups * in->lay.M * 8;
     if (bytes < need) return fail(ICM_ENOMEM, "fold buffer too small");
     icm_scores *sc = new (std::nothrow) icm_scores();
     if (!sc) return fail(ICM_ENOMEM, "host allocation");
-    cudaError_t e = launch_fold(c, to_dev(in->lay), in->dev, in->n_eyes, (uint64_t *)dev_out, (cudaStream_t)stream);
+    cudaError_t e = launch_fold(c, to_dev(in->lay), in->dev, in->n_eyes, limbs, (uint64_t *)dev_out, (cudaStream_t)stream);
     if (e != cudaSuccess) { delete sc; return fail(ICM_ECUDA, std::string("fold: ") + cudaGetErrorString(e)); }
     sc->ctx = c; sc->lay = in->lay; sc->n_eyes = in->n_eyes; sc->n_cols = in->n_eyes * groups; sc->folded = 1;
+    sc->rescaled = in->rescaled;
     sc->dev = (uint64_t *)dev_out; sc->bytes = bytes;
     *out = sc;
     return ICM_OK;
@@ -458,7 +490,7 @@ void icm_scores_destroy(icm_scores *s) { delete s; }
 
 icm_status icm_scores_shape(const icm_scores *s, size_t *n_limbs, size_t *n_cols, size_t *m_rows) {
     if (!s) return fail(ICM_EINVAL, "null argument");
-    if (n_limbs) *n_limbs = s->ctx->p.n_limbs;
+    if (n_limbs) *n_limbs = s->rescaled ? s->ctx->p.n_limbs_q : s->ctx->p.n_limbs;
     if (n_cols) *n_cols = s->n_cols;
     if (m_rows) *m_rows = s->lay.M;
     return ICM_OK;
@@ -468,8 +500,35 @@ icm_status icm_decrypt_scores(icm_ctx *c, const icm_scores *s, int64_t *dev_num,
     if (!c || !s || !dev_num) return fail(ICM_EINVAL, "null argument");
     if (!c->have_keys) return fail(ICM_EINVAL, "icm_keygen has not run");
     if (n < (size_t)s->n_cols * s->lay.n_real) return fail(ICM_ENOMEM, "numerator buffer too small");
-    cudaError_t e = launch_decrypt(c, to_dev(s->lay), s->dev, s->n_cols, dev_num, (cudaStream_t)stream);
+    cudaError_t e = launch_decrypt(c, to_dev(s->lay), s->dev, s->n_cols, s->rescaled != 0, dev_num,
+                                   (cudaStream_t)stream);
     if (e != cudaSuccess) return fail(ICM_ECUDA, std::string("decrypt: ") + cudaGetErrorString(e));
+    return ICM_OK;
+}
+
+icm_status icm_rescale_bytes(const icm_scores *in, size_t *bytes) {
+    if (!in || !bytes) return fail(ICM_EINVAL, "null argument");
+    *bytes = (size_t)in->ctx->p.n_limbs_q * in->n_cols * in->lay.M * 8;
+    return ICM_OK;
+}
+
+icm_status icm_rescale(icm_ctx *c, const icm_scores *in, void *dev_out, size_t bytes, void *stream, icm_scores **out) {
+    if (!c || !in || !dev_out || !out) return fail(ICM_EINVAL, "null argument");
+    if (in->ctx != c) return fail(ICM_EINVAL, "handle from another context");
+    if (in->rescaled) return fail(ICM_EINVAL, "scores are already rescaled");
+    if (c->p.n_limbs_q >= c->p.n_limbs) return fail(ICM_EINVAL, "no limb of Q' to drop");
+    size_t need;
+    icm_rescale_bytes(in, &need);
+    if (bytes < need) return fail(ICM_ENOMEM, "rescale buffer too small");
+    icm_scores *sc = new (std::nothrow) icm_scores();
+    if (!sc) return fail(ICM_ENOMEM, "host allocation");
+    cudaError_t e = launch_rescale(c, in->dev, (uint64_t)in->n_cols * in->lay.M, (uint64_t *)dev_out,
+                                   (cudaStream_t)stream);
+    if (e != cudaSuccess) { delete sc; return fail(ICM_ECUDA, std::string("rescale: ") + cudaGetErrorString(e)); }
+    *sc = *in;
+    sc->rescaled = 1;
+    sc->dev = (uint64_t *)dev_out; sc->bytes = bytes;
+    *out = sc;
     return ICM_OK;
 }
 

@@ -10,8 +10,18 @@
 //
 // Decryption (Section 2.2.2, Dec(a, b) = a * sk + b per b-block): D = C_b + s_{db,t} * C_a modulo
 // every q_l, then a fixed-point CRT gives D / Q_db modulo 1, and the numerator is the nearest
-// integer to D_centred / (Q' Delta).
+// integer to D_centred / (Q' Delta).  After rescaling the same holds modulo Q with scale Delta.
+//
+// Rescaling by Q' (Section 2.2.2, Maintenance: RS divides by a modulus factor and rounds, here
+// the factor Q' = q_Lq ... q_{L-1}, so the scores leave at the query modulus Q with scale Delta):
+// per coefficient, yh_i = x_i (Q'/q_i)^-1 mod q_i for the limbs of Q', the correction
+// v = floor((sum_i F_i + 2^63) / 2^64) from the 64-bit fixed-point fractions
+// F_i = floor(yh_i floor(2^128 / q_i) / 2^64) (integer arithmetic only), the centred
+// y = sum_i yh_i (Q'/q_i) - v Q' = x mod Q', and x'_j = (x_j - y mod q_j) Q'^-1 mod q_j for the
+// limbs of Q.  HBM-bound: reads L words and writes L_q words per coefficient.
 #include "icm_internal.h"
+
+#include <algorithm>
 
 namespace {
 
@@ -119,16 +129,58 @@ __global__ void __launch_bounds__(256) k_decrypt(DecArgs a) {
     a.num[(size_t)j * a.lay.n_real + r] = (int64_t)rint(frac * a.crt.q_over_delta);
 }
 
+struct RsArgs {
+    icm::RescaleConsts k;
+    const uint64_t *in;    // [L][n]
+    uint64_t *out;         // [Lq][n]
+    uint64_t n;
+};
+
+// One thread per coefficient (grid-stride); consecutive threads read consecutive words of a limb.
+__global__ void __launch_bounds__(256) k_rescale(const __grid_constant__ RsArgs a) {
+    const uint32_t L = a.k.L, Lq = a.k.Lq;
+    for (uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; c < a.n; c += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t yh[ICM_MAX_LIMBS];
+        uint64_t slo = 0, shi = 0;                                 // sum of the F_i, 128-bit
+        for (uint32_t i = Lq; i < L; ++i) {
+            const uint64_t q = a.k.q[i];
+            yh[i] = mulmod_shoup(a.in[(size_t)i * a.n + c], a.k.yinv[i], a.k.yinvs[i], q);
+            // F_i = yh rhi + floor(yh rlo / 2^64): exact, and < 2^64 because yh < q_i
+            const uint64_t f = yh[i] * a.k.rhi[i] + __umul64hi(yh[i], a.k.rlo[i]);
+            slo += f;
+            shi += slo < f ? 1 : 0;
+        }
+        const uint64_t v = shi + ((slo >> 63) & 1);                // floor((S + 2^63) / 2^64)
+        for (uint32_t j = 0; j < Lq; ++j) {
+            const uint64_t q = a.k.q[j];
+            uint64_t y = 0;
+            for (uint32_t i = Lq; i < L; ++i) y = add_mod(y, mulmod_shoup(yh[i], a.k.w[j][i], a.k.ws[j][i], q), q);
+            y = sub_mod(y, mulmod_shoup(v, a.k.qp[j], a.k.qps[j], q), q);
+            const uint64_t d = sub_mod(a.in[(size_t)j * a.n + c], y, q);
+            a.out[(size_t)j * a.n + c] = mulmod_shoup(d, a.k.qpinv[j], a.k.qpinvs[j], q);
+        }
+    }
+}
+
 }  // namespace
 
 namespace icm {
 
-cudaError_t launch_fold(const icm_ctx *c, const LayoutDev &lay, const uint64_t *d_in, uint32_t n_eyes,
+cudaError_t launch_rescale(const icm_ctx *c, const uint64_t *d_in, uint64_t n, uint64_t *d_out, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    RsArgs a{c->rs, d_in, d_out, n};
+    const unsigned blocks = (unsigned)std::min<uint64_t>((n + 255) / 256, 152ull * 16);
+    k_rescale<<<blocks, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+
+cudaError_t launch_fold(const icm_ctx *c, const LayoutDev &lay, const uint64_t *d_in, uint32_t n_eyes, uint32_t limbs,
                         uint64_t *d_out, cudaStream_t st) {
     FoldArgs a{};
     a.lay = lay; a.rho = c->p.rho; a.k = c->p.fold_k;
     a.groups = (c->p.rho + c->p.fold_k - 1) / c->p.fold_k;
-    a.n_eyes = n_eyes; a.L = c->p.n_limbs;
+    a.n_eyes = n_eyes; a.L = limbs;                 // the first `limbs` primes (Q's come first)
     for (uint32_t l = 0; l < a.L; ++l) { a.q[l] = c->q[l]; a.r64[l] = c->lt.r64[l]; }
     a.in = d_in; a.out = d_out;
     if (n_eyes == 0 || lay.M == 0) return cudaSuccess;
@@ -138,11 +190,11 @@ cudaError_t launch_fold(const icm_ctx *c, const LayoutDev &lay, const uint64_t *
 }
 
 cudaError_t launch_decrypt(const icm_ctx *c, const LayoutDev &lay, const uint64_t *d_scores, uint32_t n_cols,
-                           int64_t *d_num, cudaStream_t st) {
+                           bool rescaled, int64_t *d_num, cudaStream_t st) {
     DecArgs a{};
-    a.lay = lay; a.L = c->p.n_limbs; a.h = c->p.hamming_weight; a.n_cols = n_cols;
+    a.lay = lay; a.L = rescaled ? c->p.n_limbs_q : c->p.n_limbs; a.h = c->p.hamming_weight; a.n_cols = n_cols;
     for (uint32_t l = 0; l < a.L; ++l) { a.q[l] = c->q[l]; a.r64[l] = c->lt.r64[l]; }
-    a.crt = c->crt;
+    a.crt = rescaled ? c->crt_q : c->crt;
     a.sdb_pos = c->d_sdb_pos; a.sdb_sgn = c->d_sdb_sgn;
     a.sc = d_scores; a.num = d_num;
     if (n_cols == 0 || lay.n_real == 0) return cudaSuccess;

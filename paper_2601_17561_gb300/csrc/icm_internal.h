@@ -28,6 +28,18 @@ struct CrtDecode {               // constants of the fixed-point CRT decoding (d
     double q_over_delta;             // Q / Delta
 };
 
+// Rescaling by Q' (x' = round(x / Q') mod Q, base conversion from the limbs of Q' to those of Q):
+// for the limbs i of Q' (i >= Lq) yinv_i = (Q'/q_i)^-1 mod q_i; for the limbs j of Q (j < Lq)
+// w[j][i] = (Q'/q_i) mod q_j, qp_j = Q' mod q_j and qpinv_j = Q'^-1 mod q_j; Shoup companions.
+struct RescaleConsts {
+    uint32_t L, Lq;
+    uint64_t q[ICM_MAX_LIMBS];
+    uint64_t yinv[ICM_MAX_LIMBS], yinvs[ICM_MAX_LIMBS];
+    uint64_t rhi[ICM_MAX_LIMBS], rlo[ICM_MAX_LIMBS];       // floor(2^128 / q_i), high and low words
+    uint64_t w[ICM_MAX_LIMBS][ICM_MAX_LIMBS], ws[ICM_MAX_LIMBS][ICM_MAX_LIMBS];
+    uint64_t qp[ICM_MAX_LIMBS], qps[ICM_MAX_LIMBS], qpinv[ICM_MAX_LIMBS], qpinvs[ICM_MAX_LIMBS];
+};
+
 }  // namespace icm
 
 struct icm_ctx {
@@ -35,7 +47,9 @@ struct icm_ctx {
     uint32_t N_db, N_q, K, n_qblk;      // ring degrees, K = d2 + N_q, n_qblk = d2 / N_q
     std::vector<uint64_t> q;            // primes
     LimbTable lt;
-    icm::CrtDecode crt;
+    icm::CrtDecode crt;                 // decoding at modulus Q_db (L limbs, scale Q' Delta)
+    icm::CrtDecode crt_q;               // decoding at modulus Q after rescaling (L_q limbs, scale Delta)
+    icm::RescaleConsts rs;
     std::vector<uint64_t> qp_mod;       // Q' mod q_l (gadget factor)
     std::vector<uint64_t> qp_mods;      // Shoup companions
     std::vector<uint64_t> delta_mod;    // Delta mod q_l
@@ -86,7 +100,8 @@ struct icm_scores {
     DbLayout lay;
     uint32_t n_eyes, n_cols;
     int folded;
-    uint64_t *dev;             // [L][n_cols][M]
+    int rescaled;              // 1: rescaled by Q' (modulus Q, L_q limbs, scale Delta)
+    uint64_t *dev;             // [limbs][n_cols][M], limbs = L, or L_q when rescaled
     size_t bytes;
 };
 
@@ -110,10 +125,12 @@ cudaError_t launch_query_extend(const icm_ctx *c, const uint64_t *d_ct, uint32_t
                                 cudaStream_t st);
 cudaError_t launch_ppmm_u64(const LimbTable &lt, const uint64_t *A, const uint64_t *B, uint64_t *C,
                             uint64_t M, uint64_t N, uint64_t K, bool a_digits, cudaStream_t st);
-cudaError_t launch_fold(const icm_ctx *c, const LayoutDev &lay, const uint64_t *d_in, uint32_t n_eyes,
+cudaError_t launch_fold(const icm_ctx *c, const LayoutDev &lay, const uint64_t *d_in, uint32_t n_eyes, uint32_t limbs,
                         uint64_t *d_out, cudaStream_t st);
 cudaError_t launch_decrypt(const icm_ctx *c, const LayoutDev &lay, const uint64_t *d_scores, uint32_t n_cols,
-                           int64_t *d_num, cudaStream_t st);
+                           bool rescaled, int64_t *d_num, cudaStream_t st);
+// Rescaling by Q' of n coefficients per limb: [L][n] at modulus Q_db -> [L_q][n] at modulus Q.
+cudaError_t launch_rescale(const icm_ctx *c, const uint64_t *d_in, uint64_t n, uint64_t *d_out, cudaStream_t st);
 
 LimbTable make_limb_table(const std::vector<uint64_t> &q);
 uint64_t shoup_of(uint64_t w, uint64_t q);

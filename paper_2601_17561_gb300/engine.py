@@ -79,6 +79,7 @@ class Engine:
         self.ctx = C.icm_ctx_create(self.params)
         self.keyed = False
         self.L = n_limbs
+        self.Lq = n_limbs_q
         self.rho = rho
         self.fold_k = fold_k
         self.K = d2 + (1 << log_n_q)
@@ -148,6 +149,13 @@ class Engine:
         buf = out if out is not None else _u8(nbytes, self.device)
         h = C.icm_fold(self.ctx, s.handle, buf, nbytes, stream)
         return Scores(h, buf, C.icm_scores_shape(h), s.n_eyes, True, s.db)
+
+    def rescale(self, s: Scores, stream=None, out: torch.Tensor = None) -> Scores:
+        """Scores at modulus Q_db -> scores at the query modulus Q (L_q limbs, scale Delta)."""
+        nbytes = C.icm_rescale_bytes(s.handle)
+        buf = out if out is not None else _u8(nbytes, self.device)
+        h = C.icm_rescale(self.ctx, s.handle, buf, nbytes, stream)
+        return Scores(h, buf, C.icm_scores_shape(h), s.n_eyes, s.folded, s.db)
 
     # -------------------------------------------------------------------- batching form
     def match_batch(self, dbs, q: Query, stream=None, outs=None, ws: torch.Tensor = None):

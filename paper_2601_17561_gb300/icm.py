@@ -59,6 +59,8 @@ _SIGS = {
     "icm_scores_destroy": (None, [_vp]),
     "icm_scores_shape": (_i32, [_vp, ctypes.POINTER(_sz), ctypes.POINTER(_sz), ctypes.POINTER(_sz)]),
     "icm_decrypt_scores": (_i32, [_vp, _vp, _vp, _sz, _vp]),
+    "icm_rescale_bytes": (_i32, [_vp, ctypes.POINTER(_sz)]),
+    "icm_rescale": (_i32, [_vp, _vp, _vp, _sz, _vp, ctypes.POINTER(_vp)]),
     "icm_ppmm_workspace_bytes": (_i32, [_i32, _u32, _sz, _sz, _sz, ctypes.POINTER(_sz)]),
     "icm_ppmm": (_i32, [_i32, _vp, _u32, _vp, _vp, _vp, _sz, _sz, _sz, _vp, _sz, _vp]),
     "icm_sync": (_i32, [_vp, _u32]),
@@ -219,6 +221,18 @@ def icm_match(ctx, db, q, dev_out, nbytes, dev_ws=None, ws_bytes=0, stream=None)
 def icm_fold(ctx, scores, dev_out, nbytes, stream=None):
     h = ctypes.c_void_p()
     _check(lib().icm_fold(ctx, scores, _ptr(dev_out), nbytes, _stream(stream), ctypes.byref(h)), "icm_fold")
+    return h
+
+
+def icm_rescale_bytes(scores):
+    n = _sz()
+    _check(lib().icm_rescale_bytes(scores, ctypes.byref(n)), "icm_rescale_bytes")
+    return n.value
+
+
+def icm_rescale(ctx, scores, dev_out, nbytes, stream=None):
+    h = _vp()
+    _check(lib().icm_rescale(ctx, scores, _ptr(dev_out), nbytes, _stream(stream), ctypes.byref(h)), "icm_rescale")
     return h
 
 

@@ -278,3 +278,47 @@ def test_ccmm_tcgen05_odd_modulus_count():
     rows = np.unique(np.concatenate([np.arange(0, 8), np.arange(M - 16, M)]))
     ref = O.ppmm(P.q, np.ascontiguousarray(A[:, rows, :]), Bq)
     assert np.array_equal(res[1][:, :, rows], ref)
+
+
+# ----------------------------------------------------------------------------- rescaling by Q'
+
+def test_rescale_bit_exact(tiny, gpu_run):
+    """Rescaling by Q' on the GPU gives the oracle's residues at modulus Q (the correction v is
+    decided in IEEE double on both sides), for the CCMM result and for the folded scores, and the
+    fold of rescaled scores equals the oracle's fold at the rescaled level."""
+    P, eng = tiny["P"], gpu_run["eng"]
+    r = eng.rescale(gpu_run["s"])
+    rf = eng.rescale(gpu_run["f"])
+    fr = eng.fold(r)
+    torch.cuda.synchronize()
+    R = O.rescale(P, tiny["C"])
+    assert r.shape[0] == P.n_limbs_q and np.array_equal(r.residues(), R)
+    assert np.array_equal(rf.residues(), O.rescale(P, tiny["F"]))
+    Pq = O.Params(**{**O.TINY, "n_limbs": P.n_limbs_q})
+    W = tiny["W"]
+    assert np.array_equal(fr.residues(), O.fold(Pq, R, tiny["ids"], n_eyes=W.q_codes.shape[0],
+                                               n_real=W.db_codes.shape[0]))
+
+
+def test_rescaled_decryption_exact(tiny, gpu_run):
+    """Decryption at modulus Q with scale Delta of the rescaled CCMM result gives the cleartext
+    inner products exactly; the rescaled fold decrypts like the full-level fold."""
+    eng = gpu_run["eng"]
+    dec = eng.decrypt(eng.rescale(gpu_run["s"]))
+    fdec = eng.decrypt(eng.rescale(gpu_run["f"]))
+    torch.cuda.synchronize()
+    assert np.array_equal(dec.cpu().numpy(), tiny["inner"])
+    assert np.array_equal(fdec.cpu().numpy(), gpu_run["fdec"])
+
+
+def test_rescale_rejects_misuse(gpu_run):
+    from paper_2601_17561_gb300 import icm as C
+    eng = gpu_run["eng"]
+    r = eng.rescale(gpu_run["s"])
+    with pytest.raises(C.IcmError) as e:
+        eng.rescale(r)
+    assert e.value.status == C.ICM_EINVAL
+    small = torch.empty(8, dtype=torch.uint8, device="cuda")
+    with pytest.raises(C.IcmError) as e:
+        C.icm_rescale(eng.ctx, gpu_run["s"].handle, small, 8)
+    assert e.value.status == C.ICM_ENOMEM

@@ -369,17 +369,17 @@ def test_rescale_is_rounded_division(P):
     xs += [(k * Qp + e) % Qdb for k in ks for e in es] + [0, Qdb - 1, Qp // 2, Qp // 2 + 1]
     C = np.array([[x % ql for x in xs] for ql in P.q], np.uint64)
     got = O.rescale(P, C)
-    # exact nearest integer; within 2^-40 of a half-integer the double-precision correction may
-    # take either neighbour (x = floor(Q'/2) is such a case: x / Q' = 1/2 - 1/(2 Q'))
+    # exact nearest integer; within (L - L_q) 2^-64 of a half-integer the fixed-point correction
+    # may take either neighbour (x = floor(Q'/2) is such a case: x / Q' = 1/2 - 1/(2 Q'))
     for idx, x in enumerate(xs):
         want = (2 * x + Qp) // (2 * Qp)
-        near_tie = abs(2 * (x % Qp) - Qp) < (Qp >> 40)
+        near_tie = abs(2 * (x % Qp) - Qp) < (Qp >> 60)
         cands = [want, want - 1, want + 1] if near_tie else [want]
         res = [int(got[j, idx]) for j in range(P.n_limbs_q)]
         assert any(res == [(c % Q) % qj for qj in P.q[: P.n_limbs_q]] for c in cands), (idx, x)
         if not near_tie:
             assert res == [(want % Q) % qj for qj in P.q[: P.n_limbs_q]]
-    assert any(abs(2 * (x % Qp) - Qp) < (Qp >> 40) for x in xs)        # the tie window is exercised
+    assert any(abs(2 * (x % Qp) - Qp) < (Qp >> 60) for x in xs)        # the tie window is exercised
     # the closed-form cases directly: k Q' + e rounds to k (|e| <= Q'/3, away from the ties)
     for k in ks:
         for e in es:
