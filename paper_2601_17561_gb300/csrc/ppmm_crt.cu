@@ -270,29 +270,47 @@ struct P2Args {
     icm::I8Consts k;
 };
 
+// Phase 2: C mod q = sum_i y_i (M/m_i mod q) - kappa (M mod q) with y_i = c_i (M/m_i)^-1 mod m_i
+// (one multiply-high division: c_i yinv_i < 2^16) and kappa = round(sum_i y_i / m_i).  Each thread
+// takes V consecutive rows of one column (V = 4: one 4-byte load per modulus plane, when the row
+// count keeps those words aligned).
+template <int V>
 __global__ void __launch_bounds__(256) k_crt_combine(P2Args p) {
-    const uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;   // (column, row) within the round
     const uint32_t l = blockIdx.y;
     const uint64_t Mall = p.tab.row0[p.tab.n];
     const uint64_t cnt = p.nch * Mall;
-    if (idx >= cnt) return;
-    const uint64_t col = idx / Mall, grow = idx % Mall;
-    uint32_t c = 0;
-    while (c + 1 < p.tab.n && grow >= p.tab.row0[c + 1]) ++c;
-    const uint64_t row = grow - p.tab.row0[c], M = p.tab.M[c];
     const uint32_t r = p.k.n_mod;
     const uint64_t q = p.k.q[l];
+    const uint64_t idx = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * V;     // (column, row) within the round
+    if (idx >= cnt) return;
+    const uint64_t col = idx / Mall, grow0 = idx % Mall;
     const uint8_t *Rl = p.R + (size_t)l * r * cnt + idx;
-    uint64_t S = 0;
-    float F = 0.f;
+    uint64_t S[V];
+    float F[V];
+#pragma unroll
+    for (int e = 0; e < V; ++e) { S[e] = 0; F[e] = 0.f; }
     for (uint32_t i = 0; i < r; ++i) {
-        const uint32_t c = Rl[(size_t)i * cnt];
-        const uint32_t y = (c * (uint32_t)p.k.yinv[i]) % (uint32_t)p.k.mod[i];
-        S = add_mod(S, mulmod_shoup(y, p.k.W[l][i], p.k.Ws[l][i], q), q);
-        F += (float)y * p.k.inv_m[i];
+        const uint32_t w = V == 4 ? *reinterpret_cast<const uint32_t *>(Rl + (size_t)i * cnt) : Rl[(size_t)i * cnt];
+        const uint32_t yinv = (uint32_t)p.k.yinv[i], m = (uint32_t)p.k.mod[i], magic = p.k.magic[i];
+        const uint64_t W = p.k.W[l][i], Ws = p.k.Ws[l][i];
+        const float inv_m = p.k.inv_m[i];
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+            const uint32_t x = ((w >> (8 * e)) & 0xFF) * yinv;
+            const uint32_t y = x - __umulhi(x, magic) * m;
+            S[e] = add_mod(S[e], mulmod_shoup(y, W, Ws, q), q);
+            F[e] += (float)y * inv_m;
+        }
     }
-    const uint64_t kappa = (uint64_t)__float2int_rn(F);
-    p.tab.C[c][((size_t)l * p.N + p.n0 + col) * M + row] = sub_mod(S, mulmod_shoup(kappa, p.k.Mq[l], p.k.Mqs[l], q), q);
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+        const uint64_t grow = grow0 + e;
+        uint32_t c = 0;
+        while (c + 1 < p.tab.n && grow >= p.tab.row0[c + 1]) ++c;
+        const uint64_t row = grow - p.tab.row0[c], M = p.tab.M[c];
+        const uint64_t kappa = (uint64_t)__float2int_rn(F[e]);
+        p.tab.C[c][((size_t)l * p.N + p.n0 + col) * M + row] = sub_mod(S[e], mulmod_shoup(kappa, p.k.Mq[l], p.k.Mqs[l], q), q);
+    }
 }
 
 // int8 residue planes of the query operand: [L][r][N][Kp], zero padded.
@@ -435,7 +453,12 @@ cudaError_t launch_crt_combine(const I8Consts &k, const ChunkTab &tab, const voi
                                uint64_t nch, cudaStream_t st) {
     const uint64_t Mall = tab.row0[tab.n];
     P2Args b{tab, reinterpret_cast<const uint8_t *>(scratch), N, n0, nch, k};
-    k_crt_combine<<<dim3((unsigned)((nch * Mall + 255) / 256), k.n_limbs), 256, 0, st>>>(b);
+    if ((Mall & 3) == 0) {
+        const uint64_t threads = nch * Mall / 4;
+        k_crt_combine<4><<<dim3((unsigned)((threads + 255) / 256), k.n_limbs), 256, 0, st>>>(b);
+    } else {
+        k_crt_combine<1><<<dim3((unsigned)((nch * Mall + 255) / 256), k.n_limbs), 256, 0, st>>>(b);
+    }
     return cudaGetLastError();
 }
 
