@@ -397,7 +397,7 @@ def main():
     gemm_avg_s = statistics.mean(gemm_ms) / 1e3
     peaks = measured_peaks()
     f = C.FORMS[args.form]
-    tc = tune is not None and tune.get("chosen") in (1, 2, 3, 4, 5, 6)
+    tc = tune is not None and tune.get("chosen") in (1, 2, 3, 4, 5)
     if args.form == "u64":
         ops = 4.0 * M * n_cols * K * L                     # IMAD.WIDE per launch (2 x 2 30-bit limb products)
         sm_max = peaks.get("sm_max_mhz", 2070.0)

@@ -226,8 +226,8 @@ void icm_plan_destroy(icm_plan *plan);
  * tcgen05 kernel (tensor-memory accumulators, TMA-fed, one modulus on 512 columns per block;
  * needs an even K, else variant 0 runs): 1 = 16 converter warps, 2 = 16 converter warps with a
  * progress bound between blocks (cooperative launch), 3 = 8 converter warps, 4 = 8 converter
- * warps with the progress bound, 5 = 2-SM MMA over clusters of two blocks (256 rows per pair),
- * 6 = 12 converter warps with 6 operand slots.  Results are identical; only speed differs. */
+ * warps with the progress bound, 5 = 2-SM MMA over clusters of two blocks (256 rows per pair).
+ * Results are identical; only speed differs. */
 icm_status icm_ctx_set_variant(icm_ctx *ctx, int variant);
 /* Device status word shared by the library's kernels: ICM_OK, or ICM_ETIMEOUT once a kernel gave
  * up one of its bounded waits (the kernel then stopped early, so its outputs are invalid).  Reads
@@ -237,7 +237,7 @@ icm_status icm_device_status(int clear);
 /* Autotuner: times every kernel variant of the CRT product on the caller's batch (one
  * icm_match_batch per variant, CUDA events on `stream`), keeps the fastest for the context and
  * reports it (0 for forms with a single variant).  ms_per_choice (optional) receives the time of
- * each variant in the order 128, 256 (mma.sync), then 1 to 6 (tcgen05, fp16 form only). */
+ * each variant in the order 128, 256 (mma.sync), then 1 to 5 (tcgen05, fp16 form only). */
 icm_status icm_autotune(icm_ctx *ctx, const icm_db *const *dbs, size_t n_dbs, const icm_query *q,
                         void *const *dev_outs, const size_t *out_bytes, void *dev_ws, size_t ws_bytes, void *stream,
                         int *best_tile_n, float *ms_per_choice, size_t n_choices);

@@ -153,8 +153,8 @@ icm_status icm_autotune(icm_ctx *c, const icm_db *const *dbs, size_t n_dbs, cons
                         float *ms_per_choice, size_t n_choices) {
     if (!c || !q || !best_tile_n) return api_fail(ICM_EINVAL, "bad arguments");
     if (!crt_form(q->form)) { *best_tile_n = 0; return ICM_OK; }      // single kernel variant
-    const int choices[8] = {128, 256, 1, 2, 3, 4, 5, 6};
-    const int n_var = q->form == ICM_FORM_F16_CRT && crt_tc_supported(c->K) ? 8 : 2;
+    const int choices[7] = {128, 256, 1, 2, 3, 4, 5};
+    const int n_var = q->form == ICM_FORM_F16_CRT && crt_tc_supported(c->K) ? 7 : 2;
     float best_ms = 1e30f;
     int best = c->crt_bn;
     cudaStream_t st = (cudaStream_t)stream;
@@ -187,7 +187,7 @@ icm_status icm_autotune(icm_ctx *c, const icm_db *const *dbs, size_t n_dbs, cons
 
 icm_status icm_ctx_set_variant(icm_ctx *c, int variant) {
     if (!c || (variant != 0 && !crt_tc_variant(variant) && variant != 128 && variant != 256))
-        return api_fail(ICM_EINVAL, "variant must be 0, 1..6, 128 or 256");
+        return api_fail(ICM_EINVAL, "variant must be 0, 1..5, 128 or 256");
     c->crt_bn = variant == 0 ? 256 : variant;
     return ICM_OK;
 }

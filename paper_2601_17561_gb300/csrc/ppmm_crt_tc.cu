@@ -749,7 +749,6 @@ namespace icm {
 #define ICM_TC_V3 8, false, false, 4, 8
 #define ICM_TC_V4 8, true, false, 4, 8
 #define ICM_TC_V5 8, false, true, 4, 8
-#define ICM_TC_V6 12, false, false, 6, 6
 
 cudaError_t crt_tc_set_attributes() {
     const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
@@ -758,7 +757,6 @@ cudaError_t crt_tc_set_attributes() {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_crt_tc<ICM_TC_V3>, attr, Ring<4, 8>::SMEM);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_crt_tc<ICM_TC_V4>, attr, Ring<4, 8>::SMEM);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_crt_tc<ICM_TC_V5>, attr, Ring<4, 8>::SMEM);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_crt_tc<ICM_TC_V6>, attr, Ring<6, 6>::SMEM);
     return e;
 }
 
@@ -866,8 +864,7 @@ cudaError_t launch_ppmm_crt_tc(const I8Consts &k, const ChunkTab &tab, const voi
             cfg.gridDim = dim3((unsigned)(2 * n_cl));
             e = cudaLaunchKernelEx(&cfg, k_crt_tc<ICM_TC_V5>, a);
         } else {
-            if (variant == 6) k_crt_tc<ICM_TC_V6><<<(unsigned)grid, 12 * 32 + 128, Ring<6, 6>::SMEM, st>>>(a);
-            else if (nwc == 16) k_crt_tc<ICM_TC_V1><<<(unsigned)grid, 16 * 32 + 128, Ring<4, 8>::SMEM, st>>>(a);
+            if (nwc == 16) k_crt_tc<ICM_TC_V1><<<(unsigned)grid, 16 * 32 + 128, Ring<4, 8>::SMEM, st>>>(a);
             else k_crt_tc<ICM_TC_V3><<<(unsigned)grid, 8 * 32 + 128, Ring<4, 8>::SMEM, st>>>(a);
             e = cudaGetLastError();
         }

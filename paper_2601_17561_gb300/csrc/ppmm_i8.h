@@ -55,9 +55,9 @@ cudaError_t crt_set_attributes();
 // tcgen05 kernel for the fp16 form on the balanced-digit database: 1 = 16 converter warps,
 // 2 = 16 converter warps with the progress bound between blocks, 3 = 8 converter warps,
 // 4 = 8 converter warps with the progress bound, 5 = 2-SM MMA over clusters of two blocks
-// (M = 256 per pair, 8 converter warps per block), 6 = 12 converter warps with 6 operand slots.
+// (M = 256 per pair, 8 converter warps per block).
 #define ICM_CRT_TCGEN05 1
-#define ICM_CRT_TCGEN05_LAST 6
+#define ICM_CRT_TCGEN05_LAST 5
 inline bool crt_tc_variant(int v) { return v >= ICM_CRT_TCGEN05 && v <= ICM_CRT_TCGEN05_LAST; }
 cudaError_t launch_crt_combine(const I8Consts &k, const ChunkTab &tab, const void *scratch, uint64_t N, uint64_t n0,
                                uint64_t nch, cudaStream_t st);

@@ -334,7 +334,7 @@ def icm_autotune(ctx, dbs, q, dev_outs, out_bytes, dev_ws, ws_bytes, stream=None
 
 # CRT product kernel variants in the autotuner's order (icm_autotune's ms_per_choice)
 VARIANTS = {128: "mma.sync-128", 256: "mma.sync-256", 1: "tcgen05-16w", 2: "tcgen05-16w-sync", 3: "tcgen05-8w",
-            4: "tcgen05-8w-sync", 5: "tcgen05-2sm-8w", 6: "tcgen05-12w-ring6"}
+            4: "tcgen05-8w-sync", 5: "tcgen05-2sm-8w"}
 
 
 def icm_ctx_set_variant(ctx, variant: int):
