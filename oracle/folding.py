@@ -31,7 +31,7 @@ Readings (the paper is silent or garbled here):
   - The paper counts the minimum and the maximum experiment of a trial separately; so does this
     module (four counters: each of the two values below P_f or above it).
 
-Parity status: every function here is pinned by `tests/test_oracle_pins.py` (numpy's Philox for
+Parity status: every function here is pinned by `tests/test_folding_pins.py` (numpy's Philox for
 the generator, the normal law's moments and CDF for the deviates, closed forms and brute force for
 the range and the convolution, the convolution for the Monte Carlo).
 """
@@ -196,6 +196,16 @@ def sum_law(coef, mu, sigma, k, h=2e-5, span=12.0, n_x=4_000_000):
     return k * y0 + np.arange(n) * h, np.maximum(pk, 0.0)
 
 
+def law_mass(grid, pmf, lo, hi):
+    """Pr(lo <= S < hi) from a law on a grid: each grid point's mass stands for its whole cell
+    [g - h/2, g + h/2) (the grid rounds every term to the nearest point), so a cell that straddles
+    lo or hi contributes the fraction inside."""
+    h = grid[1] - grid[0]
+    a = np.clip((grid + 0.5 * h - lo) / h, 0.0, 1.0)      # fraction of the cell at or above lo
+    b = np.clip((hi - (grid - 0.5 * h)) / h, 0.0, 1.0)    # fraction of the cell below hi
+    return float((pmf * np.clip(a + b - 1.0, 0.0, 1.0)).sum())
+
+
 def tail_probs(grid, pmf, lo, hi):
-    """(Pr(S < lo), Pr(S > hi)) from a law on a grid."""
-    return float(pmf[grid < lo].sum()), float(pmf[grid > hi].sum())
+    """(Pr(S < lo), Pr(S > hi)) from a law on a grid (cells as in law_mass)."""
+    return law_mass(grid, pmf, -np.inf, lo), law_mass(grid, pmf, hi, np.inf)
