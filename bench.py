@@ -292,6 +292,8 @@ def main():
     ap.add_argument("--variant", default="auto",
                     help="CRT product kernel: auto (autotuner), 128 / 256 (mma.sync) or 1 (tcgen05)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fold-trials", type=int, default=1 << 33,
+                    help="trials of the folding-polynomial check reported beside the step (0: skip)")
     ap.add_argument("--workload", default="paper", choices=["paper", "batching", "serving"],
                     help="paper: the headline CCMM step; batching / serving: the query-batching and "
                          "request-loop forms (one JSON line each, not the headline)")
@@ -457,6 +459,31 @@ def main():
               "peak_source": "of measured: MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "of fallback: 6.8 TB/s"}
         del q1, s1, out
 
+    # ---- cleartext folding-polynomial check (not part of the timed step): the paper's 1e12-trial
+    # experiment, scaled down; one trial draws 31 scores (8 Philox4x64-10 blocks)
+    fd = None
+    if args.fold_trials > 0:
+        from paper_2601_17561_gb300 import folding as FD
+        with torch.cuda.stream(st):
+            r = FD.fold_mc(1 << 26, seed=1, stream=st)                   # warm-up
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            FD.fold_mc(args.fold_trials, seed=2, trial0=0, out=r, stream=st)
+            b.record(st)
+            st.synchronize()
+        fms = a.elapsed_time(b)
+        rate = args.fold_trials / (fms / 1e3)
+        imadw = 8 * 10 * 2 * 4                                           # 32x32->64 partial products per trial
+        ipeak = C.icm_probe_peak(0)
+        fd = {"kernel": "k_fold_mc<7>", "trials": args.fold_trials, "ms": fms, "trials_per_s": rate,
+              "counts": [int(x) for x in r.counts.cpu()], "k": FD.FOLD_K, "n_f": FD.N_F, "p_f": FD.P_F,
+              "law": FD.NEG_LAW, "positive_interval": (0.3, 0.45),
+              "roofline": {"bound": "alu", "achieved": imadw * rate / 1e9, "peak": ipeak / 1e9, "unit": "Gop/s",
+                           "frac": imadw * rate / ipeak,
+                           "peak_source": "measured in this run: IMAD.WIDE issue-bound probe (icm_probe_peak 0)",
+                           "ops": "Philox 64x64->128 products as 4 IMAD.WIDE each, 640 per trial"}}
+        del r
+
     # ---- other forms, one timed step each on the same workload
     forms = {args.form: {"value": value, "ms_per_step": ms_per_step}}
     for other in [x for x in args.compare_forms.split(",") if x and x != args.form]:
@@ -498,7 +525,7 @@ def main():
                        "l2": "inputs larger than L2 (206 GB resident database), no flush",
                        "parallelism": "replicas" if ws == 1 else f"weak: {ws} database shards, same query"},
             "roofline": roof, "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clk,
-            "forms": forms, "variant": tune, "rescale": rs}
+            "forms": forms, "variant": tune, "rescale": rs, "fold_design": fd}
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         v, thr, sample, _ = oracle_sample(seconds_target=15.0)

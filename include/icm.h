@@ -184,9 +184,10 @@ icm_status icm_decrypt_scores(icm_ctx *ctx, const icm_scores *s, int64_t *dev_nu
 /* Rescaling by Q' (Section 2.2.2, Maintenance: RS divides a ciphertext by a modulus factor and
  * rounds): scores at modulus Q_db = Q Q' (L limbs) become scores at the query modulus Q (the
  * first L_q limbs) with scale Delta, x' = round(x / Q') mod Q for every coefficient of both
- * ciphertext parts (base conversion from the limbs of Q' with the correction decided in IEEE
- * double: a coefficient within rounding error of a half-integer may round to either neighbour,
- * inside the rescaling error).  Works on folded or unfolded scores (the fold commutes with it up
+ * ciphertext parts (base conversion from the limbs of Q' with the correction v = round(sum_i y_i /
+ * q_i) taken from 64.64-bit fixed-point terms floor(y_i floor(2^128 / q_i) / 2^64): a coefficient
+ * within (L - L_q) 2^-64 Q' of a half-integer multiple of Q' may round to either neighbour, inside the
+ * rescaling error).  Works on folded or unfolded scores (the fold commutes with it up
  * to that error) and cuts their size L / L_q times.  icm_rescale_bytes gives the size of
  * dev_out (caller-owned, [L_q][n_cols][M] u64).  Errors: ICM_EINVAL (already rescaled, L_q = L,
  * or a handle of another context), ICM_ENOMEM (dev_out too small), ICM_ECUDA. */
@@ -319,6 +320,46 @@ icm_status icm_ppmm(icm_form form, const uint64_t *q, uint32_t n_limbs, const ui
  * (serialise them, for instance on one stream).  Arguments as icm_ppmm minus the workspace. */
 icm_status icm_ppmm_noalloc(icm_form form, const uint64_t *q, uint32_t n_limbs, const uint64_t *dev_A,
                             const uint64_t *dev_B, uint64_t *dev_C, size_t M, size_t N, size_t K, void *stream);
+
+/* ---------------------------------------------------------------- folding-polynomial check ---- */
+
+/* Cleartext check of a folding polynomial (Section 4.1.2 defines a (k, N_f, P_f)-folding
+ * polynomial f by two probabilities over negative scores drawn from a law D; Appendix C.2 checks
+ * the paper's degree-7 f with 1e12 such experiments; Section 6.1 approximates D by N(0.008, 0.034^2)).
+ * Trial t draws 2k - 1 scores from D = N(mu, sigma^2) with Philox4x64-10 (Salmon et al., SC 2011)
+ * at counters (t, j, 0, 0), key (seed, 0), and the Box-Muller transform of word pairs (2p, 2p+1)
+ * (u1 = (a + 1/2) 2^-64, u2 = b 2^-64; normals 0..k-1 are x_i, normals k..2k-2 are y_i), and forms
+ * S_k = sum_i f(x_i) and S_{k-1} = sum_i f(y_i).  Scores, f and sums are computed in fp32. */
+typedef struct {
+    const double *coef;      /* host, degree + 1 values: f(x) = sum_i coef[i] x^i              */
+    uint32_t degree;         /* 0..15                                                           */
+    uint32_t k;              /* values per folded sum, 1..32 (the paper's folding capability)   */
+    double mu, sigma;        /* the law D = N(mu, sigma^2), sigma > 0                           */
+    double nf_lo, nf_hi;     /* N_f                                                             */
+    double pf_lo, pf_hi;     /* P_f                                                             */
+    double pos_lo, pos_hi;   /* P, the positive-score interval: the library finds min and max of
+                                f over it (ends and sign changes of f') in double precision     */
+    double hist_lo, hist_hi; /* histogram range of the sums                                     */
+    uint32_t n_bins;         /* 0 (no histogram) .. 8192                                        */
+    uint32_t accumulate;     /* 0: overwrite dev_counts / dev_hist; else add to them            */
+    uint64_t seed;           /* Philox key word 0                                               */
+    uint64_t trial0;         /* first trial index (runs over consecutive ranges continue a run)  */
+    uint64_t n_trials;       /* trials of this call (0 allowed)                                  */
+} icm_fold_mc_args;
+
+/* Run trials trial0 .. trial0 + n_trials - 1 on `stream`.  dev_counts (device, 6 x u64): trials
+ * with S_k < nf_lo, S_k > nf_hi, min_P f + S_{k-1} < pf_lo, min_P f + S_{k-1} > pf_hi,
+ * max_P f + S_{k-1} < pf_lo, max_P f + S_{k-1} > pf_hi.  dev_hist (device, [2][n_bins + 2] u64,
+ * may be NULL when n_bins = 0): histograms of S_k and of S_{k-1}, bin 0 below hist_lo, bins
+ * 1..n_bins of width (hist_hi - hist_lo) / n_bins, bin n_bins + 1 at or above hist_hi.  dev_sums
+ * (device, optional): n_trials pairs of float (S_k, S_{k-1}).  Device pointers 8-byte aligned.
+ * Errors: ICM_EINVAL (bad degree, k, law, interval, histogram, alignment or a trial range that
+ * wraps), ICM_ECUDA. */
+icm_status icm_fold_mc(const icm_fold_mc_args *args, uint64_t *dev_counts, uint64_t *dev_hist, float *dev_sums,
+                       void *stream);
+/* Minimum and maximum of f over [lo, hi] as icm_fold_mc takes them for P (host only). */
+icm_status icm_fold_poly_range(const double *coef, uint32_t degree, double lo, double hi, double *fmin,
+                               double *fmax);
 
 /* ---------------------------------------------------------------- measurement ---- */
 

@@ -34,6 +34,15 @@ class icm_params(ctypes.Structure):
         "hamming_weight", "log2_delta", "noise_eta")] + [("seed", ctypes.c_uint64)]
 
 
+class icm_fold_mc_args(ctypes.Structure):
+    _fields_ = [("coef", ctypes.c_void_p), ("degree", ctypes.c_uint32), ("k", ctypes.c_uint32),
+                ("mu", ctypes.c_double), ("sigma", ctypes.c_double), ("nf_lo", ctypes.c_double),
+                ("nf_hi", ctypes.c_double), ("pf_lo", ctypes.c_double), ("pf_hi", ctypes.c_double),
+                ("pos_lo", ctypes.c_double), ("pos_hi", ctypes.c_double), ("hist_lo", ctypes.c_double),
+                ("hist_hi", ctypes.c_double), ("n_bins", ctypes.c_uint32), ("accumulate", ctypes.c_uint32),
+                ("seed", ctypes.c_uint64), ("trial0", ctypes.c_uint64), ("n_trials", ctypes.c_uint64)]
+
+
 _lib = None
 _vp, _sz, _u32, _u64, _i32 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
 
@@ -83,6 +92,9 @@ _SIGS = {
     "icm_server_wait": (_i32, [_vp, _u64, _u32, ctypes.POINTER(ctypes.c_double)]),
     "icm_server_stats": (_i32, [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64), ctypes.POINTER(ctypes.c_double)]),
     "icm_server_destroy": (_i32, [_vp, _u32]),
+    "icm_fold_mc": (_i32, [ctypes.POINTER(icm_fold_mc_args), _vp, _vp, _vp, _vp]),
+    "icm_fold_poly_range": (_i32, [_vp, _u32, ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_double)]),
     "icm_autotune": (_i32, [_vp, _vp, _sz, _vp, _vp, _vp, _vp, _sz, _vp, ctypes.POINTER(_i32),
                             ctypes.POINTER(ctypes.c_float), _sz]),
 }
@@ -395,3 +407,16 @@ def icm_ppmm_noalloc(form, q, n_limbs, dev_A, dev_B, dev_C, M, N, K, stream=None
 
 def icm_sync(stream=None, timeout_ms: int = 600000):
     _check(lib().icm_sync(_stream(stream), timeout_ms), "icm_sync")
+
+
+def icm_fold_mc(args: icm_fold_mc_args, dev_counts, dev_hist=None, dev_sums=None, stream=None):
+    _check(lib().icm_fold_mc(ctypes.byref(args), _ptr(dev_counts), _ptr(dev_hist), _ptr(dev_sums), _stream(stream)),
+           "icm_fold_mc")
+
+
+def icm_fold_poly_range(coef, lo: float, hi: float):
+    c = (ctypes.c_double * len(coef))(*coef)
+    mn, mx = ctypes.c_double(), ctypes.c_double()
+    _check(lib().icm_fold_poly_range(c, len(coef) - 1, lo, hi, ctypes.byref(mn), ctypes.byref(mx)),
+           "icm_fold_poly_range")
+    return mn.value, mx.value

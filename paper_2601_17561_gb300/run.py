@@ -6,6 +6,11 @@ Workloads: tiny (4 eyes x 256 codes, ring 2^12, 3 primes < 2^50), mid (32 eyes x
 same ring and primes: about 3 GB on the device, sized for profiler captures), paper (32 eyes x
 114,688 codes, N_db = 2^14, N_q = 2^13, 8 primes < 2^60).  Each pass prepares the query,
 runs the CCMM and the fold.
+
+    python -m paper_2601_17561_gb300.run --fold-trials 268435456
+
+runs the cleartext check of the paper's folding polynomial instead (Appendix C.2 experiments on
+N(0.008, 0.034^2) scores, positive interval [0.3, 0.45]) and prints the six outlier counts.
 """
 from __future__ import annotations
 
@@ -34,8 +39,19 @@ def main(argv=None):
     ap.add_argument("--passes", type=int, default=1)
     ap.add_argument("--variant", type=int, default=None,
                     help="CRT product kernel: 1 = tcgen05, 128 / 256 = mma.sync column tile (default: library's)")
+    ap.add_argument("--fold-trials", type=int, default=0, help="run the folding-polynomial check instead")
     a = ap.parse_args(argv)
     B.build()
+    if a.fold_trials:
+        from . import folding as FD
+        for i in range(a.passes):
+            t0 = time.perf_counter()
+            r = FD.fold_mc(a.fold_trials, seed=1 + i)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            print(f"pass {i}: {dt * 1e3:.1f} ms, {a.fold_trials / dt:.3e} trials/s, counts "
+                  f"{[int(x) for x in r.counts.cpu()]}", flush=True)
+        return 0
     params, wl = WORKLOADS[a.workload]
     W = synth.make_workload(**wl)
     eng = E.Engine(**params).keygen()

@@ -99,3 +99,56 @@ def test_paper_shape_sizes(lib):
         C.icm_ctx_destroy(ctx)
     assert m == 131072
     assert nbytes == 8 * 131072 * 24576 * 8
+
+
+# ----------------------------------------------------------------------------- folding-polynomial check
+
+@pytest.mark.parametrize("lo,hi", [(0.3, 0.45), (-0.25, 0.2), (-0.3, 1.0), (0.1, 0.1), (-0.1, -0.05), (0.257, 0.496)])
+def test_fold_poly_range_agrees_with_oracle(lib, lo, hi):
+    """The library's range of f over P (ends and sign changes of f') against the oracle's
+    (roots of f' by numpy's companion matrix)."""
+    from oracle import folding as F
+    from paper_2601_17561_gb300 import folding as G
+    got = C.icm_fold_poly_range(G.FOLD_COEF_K16, lo, hi)
+    want = F.poly_range(F.PAPER_FOLD_COEF, lo, hi)
+    assert got == pytest.approx(want, rel=1e-12, abs=1e-15)
+    # a quartic with two interior minima and one interior maximum
+    q = (0.0, 0.0, -2.0, 0.0, 1.0)                      # x^4 - 2 x^2: min -1 at +-1, max 0 at 0
+    assert C.icm_fold_poly_range(q, -1.5, 1.2) == pytest.approx(F.poly_range(q, -1.5, 1.2), abs=1e-12)
+
+
+def _mc_args(**kw):
+    from paper_2601_17561_gb300 import folding as G
+    coef = kw.pop("coef", G.FOLD_COEF_K16)
+    cf = (ctypes.c_double * len(coef))(*coef)
+    base = dict(coef=ctypes.cast(cf, ctypes.c_void_p), degree=len(coef) - 1, k=16, mu=0.008, sigma=0.034,
+                nf_lo=-0.13, nf_hi=0.33, pf_lo=0.4, pf_hi=3.8, pos_lo=0.3, pos_hi=0.45, hist_lo=0.0, hist_hi=0.0,
+                n_bins=0, accumulate=0, seed=1, trial0=0, n_trials=16)
+    base.update(kw)
+    return C.icm_fold_mc_args(**base), cf
+
+
+@pytest.mark.parametrize("bad", [dict(degree=16), dict(k=0), dict(k=33), dict(sigma=0.0), dict(sigma=float("nan")),
+                                 dict(nf_lo=1.0, nf_hi=0.0), dict(pf_lo=4.0), dict(pos_lo=0.5, pos_hi=0.4),
+                                 dict(n_bins=8193), dict(n_bins=10, hist_lo=1.0, hist_hi=1.0),
+                                 dict(trial0=2**64 - 4, n_trials=8)])
+def test_fold_mc_rejects_bad_arguments(lib, bad):
+    """Rejected before any device work (no GPU needed): bad degree, k, law, intervals, histogram
+    and a trial range that wraps around 2^64."""
+    import torch
+    if torch.cuda.is_available():                               # real buffers where a GPU exists
+        buf = torch.zeros(2 * 8200, dtype=torch.int64, device="cuda")
+        counts, hist, odd = buf.data_ptr(), buf.data_ptr() + 64, buf.data_ptr() + 4
+    else:                                                       # never dereferenced: rejected first
+        counts, hist, odd = 8, 16, 12
+    a, keep = _mc_args(**bad)
+    with pytest.raises(C.IcmError) as e:
+        C.icm_fold_mc(a, counts, hist if a.n_bins else None, None, 0)
+    assert e.value.status == C.ICM_EINVAL
+    a, keep = _mc_args()
+    with pytest.raises(C.IcmError) as e:
+        C.icm_fold_mc(a, None, None, None, 0)                   # no counts buffer
+    assert e.value.status == C.ICM_EINVAL
+    with pytest.raises(C.IcmError) as e:
+        C.icm_fold_mc(a, odd, None, None, 0)                    # misaligned counts
+    assert e.value.status == C.ICM_EINVAL
