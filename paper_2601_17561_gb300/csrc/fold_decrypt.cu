@@ -136,30 +136,43 @@ struct RsArgs {
     uint64_t n;
 };
 
-// One thread per coefficient (grid-stride); consecutive threads read consecutive words of a limb.
-__global__ void __launch_bounds__(256) k_rescale(const __grid_constant__ RsArgs a) {
-    const uint32_t L = a.k.L, Lq = a.k.Lq;
-    for (uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; c < a.n; c += (uint64_t)gridDim.x * blockDim.x) {
-        uint64_t yh[ICM_MAX_LIMBS];
-        uint64_t slo = 0, shi = 0;                                 // sum of the F_i, 128-bit
-        for (uint32_t i = Lq; i < L; ++i) {
-            const uint64_t q = a.k.q[i];
-            yh[i] = mulmod_shoup(a.in[(size_t)i * a.n + c], a.k.yinv[i], a.k.yinvs[i], q);
-            // F_i = yh rhi + floor(yh rlo / 2^64): exact, and < 2^64 because yh < q_i
-            const uint64_t f = yh[i] * a.k.rhi[i] + __umul64hi(yh[i], a.k.rlo[i]);
-            slo += f;
-            shi += slo < f ? 1 : 0;
-        }
-        const uint64_t v = shi + ((slo >> 63) & 1);                // floor((S + 2^63) / 2^64)
-        for (uint32_t j = 0; j < Lq; ++j) {
-            const uint64_t q = a.k.q[j];
-            uint64_t y = 0;
-            for (uint32_t i = Lq; i < L; ++i) y = add_mod(y, mulmod_shoup(yh[i], a.k.w[j][i], a.k.ws[j][i], q), q);
-            y = sub_mod(y, mulmod_shoup(v, a.k.qp[j], a.k.qps[j], q), q);
-            const uint64_t d = sub_mod(a.in[(size_t)j * a.n + c], y, q);
-            a.out[(size_t)j * a.n + c] = mulmod_shoup(d, a.k.qpinv[j], a.k.qpinvs[j], q);
-        }
+// Rescale one coefficient c of [L][n] into [Lq][n].
+__device__ __forceinline__ void rescale_one(const icm::RescaleConsts &k, const uint64_t *in, uint64_t *out, uint64_t n,
+                                            uint64_t c) {
+    const uint32_t L = k.L, Lq = k.Lq;
+    uint64_t yh[ICM_MAX_LIMBS];
+    uint64_t slo = 0, shi = 0;                                     // sum of the F_i, 128-bit
+#pragma unroll
+    for (uint32_t i = 0; i < ICM_MAX_LIMBS; ++i) {
+        if (i < Lq || i >= L) continue;
+        const uint64_t q = k.q[i];
+        yh[i] = mulmod_shoup(in[(size_t)i * n + c], k.yinv[i], k.yinvs[i], q);
+        // F_i = yh rhi + floor(yh rlo / 2^64): exact, and < 2^64 because yh < q_i
+        const uint64_t f = yh[i] * k.rhi[i] + __umul64hi(yh[i], k.rlo[i]);
+        slo += f;
+        shi += slo < f ? 1 : 0;
     }
+    const uint64_t v = shi + ((slo >> 63) & 1);                    // floor((S + 2^63) / 2^64)
+    for (uint32_t j = 0; j < Lq; ++j) {
+        const uint64_t q = k.q[j];
+        uint64_t y = 0;
+#pragma unroll
+        for (uint32_t i = 0; i < ICM_MAX_LIMBS; ++i)
+            if (i >= Lq && i < L) y = add_mod(y, mulmod_shoup(yh[i], k.w[j][i], k.ws[j][i], q), q);
+        y = sub_mod(y, mulmod_shoup(v, k.qp[j], k.qps[j], q), q);
+        const uint64_t d = sub_mod(in[(size_t)j * n + c], y, q);
+        out[(size_t)j * n + c] = mulmod_shoup(d, k.qpinv[j], k.qpinvs[j], q);
+    }
+}
+
+// Two coefficients per thread (independent chains for latency hiding); consecutive threads read
+// consecutive words of a limb.
+__global__ void __launch_bounds__(256) k_rescale(const __grid_constant__ RsArgs a) {
+    const uint64_t c0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    const uint64_t half = (a.n + 1) / 2;
+    if (c0 >= half) return;
+    rescale_one(a.k, a.in, a.out, a.n, c0);
+    if (c0 + half < a.n) rescale_one(a.k, a.in, a.out, a.n, c0 + half);
 }
 
 }  // namespace
@@ -169,8 +182,8 @@ namespace icm {
 cudaError_t launch_rescale(const icm_ctx *c, const uint64_t *d_in, uint64_t n, uint64_t *d_out, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
     RsArgs a{c->rs, d_in, d_out, n};
-    const unsigned blocks = (unsigned)std::min<uint64_t>((n + 255) / 256, 152ull * 16);
-    k_rescale<<<blocks, 256, 0, st>>>(a);
+    const uint64_t threads = (n + 1) / 2;
+    k_rescale<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 
