@@ -277,6 +277,57 @@ def run_serving(args, dev):
     return 0
 
 
+def run_p2(args, dev):
+    """The paper's own modulus family on its per-GPU CCMM unit (Section 6.2.2; Table 2 times it at
+    259 ms on an RTX-5090): Q = prod p^2 over the 24 primes 127 <= p <= 253 (2^360.8), one database
+    slice of 2^14 rows x K = 24,576 against 32 eyes x 31 rotations = 992 columns; every modulus is
+    two int8 passes (x0 y0 over K, x0 y1 + x1 y0 over 2K).  One step = three icm_ppmm calls of 8
+    moduli; random residues below 127^2 so one operand pair serves every modulus."""
+    import torch
+    from paper_2601_17561_gb300 import engine as E
+    from paper_2601_17561_gb300 import icm as C
+    ps = [p for p in range(127, 254) if all(p % d for d in range(2, int(p ** 0.5) + 1))]
+    M, N, K = 1 << 14, 992, 24576
+    g = torch.Generator(device=dev).manual_seed(1)
+    A = torch.randint(0, 127 * 127, (8, M, K), device=dev, dtype=torch.int64, generator=g)
+    Bm = torch.randint(0, 127 * 127, (8, N, K), device=dev, dtype=torch.int64, generator=g)
+    Cm = torch.empty((8, N, M), device=dev, dtype=torch.int64)
+    groups = [[p * p for p in ps[i:i + 8]] for i in (0, 8, 16)]
+    ws_bytes = C.icm_ppmm_workspace_bytes(C.ICM_FORM_I8_P2, 8, M, N, K)
+    ws = E._u8(ws_bytes, dev)
+    st = torch.cuda.Stream(device=dev)
+
+    def step():
+        for q in groups:
+            C.icm_ppmm(C.ICM_FORM_I8_P2, q, 8, A, Bm, Cm, M, N, K, ws, ws_bytes, st)
+
+    with torch.cuda.stream(st):
+        for _ in range(max(1, args.warmup)):
+            step()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        for _ in range(args.steps):
+            step()
+        b.record(st)
+        st.synchronize()
+    ms = a.elapsed_time(b) / args.steps
+    ops = 2.0 * M * N * 3 * K * len(ps)
+    peak = 2.0 * C.icm_probe_peak(1)
+    line = {"metric": "paper's p^2 modulus family: ms per CCMM slice (2^14 rows x 24,576 x 992, 24 moduli p^2)",
+            "value": ms, "unit": "ms", "higher_is_better": False, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "data": "synthetic", "dtype": "s8",
+            "config": {"workload": "one database slice: M = 16,384, K = 24,576, N = 992; Q = prod p^2, 127 <= p <= 253 "
+                                   "(24 moduli, 2^360.8); 3 x icm_ppmm of 8 moduli", "form": "i8_p2"},
+            "paper_ms_rtx5090": 259.0,
+            "roofline": {"bound": "tensor", "kernel": "k_ppmm_p2", "achieved": ops / (ms / 1e3) / 1e12,
+                         "peak": peak / 1e12, "unit": "TOP/s", "frac": ops / (ms / 1e3) / peak,
+                         "peak_source": "measured in this run: int8 mma.sync.m16n8k32 issue-bound probe "
+                                        "(no tcgen05 int8 on sm_103a)",
+                         "ops": "2 x M x N x 3K x 24 int8 operations (passes of K and 2K per modulus)"}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # ------------------------------------------------------------------------------ GPU arm
 
 def main():
@@ -294,9 +345,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fold-trials", type=int, default=1 << 33,
                     help="trials of the folding-polynomial check reported beside the step (0: skip)")
-    ap.add_argument("--workload", default="paper", choices=["paper", "batching", "serving"],
+    ap.add_argument("--workload", default="paper", choices=["paper", "batching", "serving", "p2"],
                     help="paper: the headline CCMM step; batching / serving: the query-batching and "
-                         "request-loop forms (one JSON line each, not the headline)")
+                         "request-loop forms; p2: the paper's p^2 modulus family on one CCMM slice "
+                         "(one JSON line each, not the headline)")
     ap.add_argument("--rates", default="2,4,8", help="serving: Poisson arrival rates (eyes/s)")
     ap.add_argument("--seconds", type=float, default=20.0, help="serving: submission time per rate")
     ap.add_argument("--window-us", type=int, default=20000, help="serving: batching window")
@@ -320,6 +372,8 @@ def main():
         return run_batching(args, dev)
     if args.workload == "serving":
         return run_serving(args, dev)
+    if args.workload == "p2":
+        return run_p2(args, dev)
     from paper_2601_17561_gb300 import engine as E
     from paper_2601_17561_gb300 import icm as C
     from paper_2601_17561_gb300 import shard

@@ -63,9 +63,14 @@ typedef enum {
                                 products per digit pair, int32 accumulation, fused recombination */
     ICM_FORM_I8_CRT = 2,     /* residues split over small pairwise-coprime moduli (<= 256),
                                 int8 tensor-core product per modulus, exact CRT back mod q_l  */
-    ICM_FORM_F16_CRT = 3     /* small-modulus residues as exact fp16 integers on fp16 tensor
+    ICM_FORM_F16_CRT = 3,    /* small-modulus residues as exact fp16 integers on fp16 tensor
                                 cores, fp32 accumulation reduced modulo m_i before it reaches
                                 2^24, residues recombined by CRT in a second pass             */
+    ICM_FORM_I8_P2 = 4       /* icm_ppmm only: the paper's own modulus family (Section 6.2.2,
+                                Q = prod p^2 over primes 127 <= p <= 253), every modulus q_l = p_l^2
+                                with odd p_l <= 253; residues split as x = x0 + p x1 into centred
+                                base-p digits, x y = x0 y0 + p (x0 y1 + x1 y0) mod p^2: two int8
+                                tensor-core passes (K, then 2K in one accumulator) per modulus */
 } icm_form;
 
 typedef struct icm_ctx icm_ctx;
@@ -302,8 +307,10 @@ icm_status icm_match_host(icm_ctx *ctx, const icm_db *db, const uint64_t *host_c
 icm_status icm_ppmm_workspace_bytes(icm_form form, uint32_t n_limbs, size_t M, size_t N, size_t K, size_t *bytes);
 
 /* Plaintext modular matrix product (PPMM, Section 2.3) on arbitrary operands:
- * dev_C[l][j][i] = sum_k dev_A[l][i][k] * dev_B[l][j][k] mod q_l, for canonical residues of
- * primes q_l < 2^60 (host array).  A: [L][M][K], B: [L][N][K], C: [L][N][M] (u64, device). */
+ * dev_C[l][j][i] = sum_k dev_A[l][i][k] * dev_B[l][j][k] mod q_l, for canonical residues of odd
+ * moduli q_l < 2^60 (host array; primes for the u64, digit and CRT forms, squares p_l^2 of odd
+ * p_l <= 253 for ICM_FORM_I8_P2, else ICM_EINVAL).  A: [L][M][K], B: [L][N][K], C: [L][N][M] (u64,
+ * device). */
 icm_status icm_ppmm(icm_form form, const uint64_t *q, uint32_t n_limbs, const uint64_t *dev_A,
                     const uint64_t *dev_B, uint64_t *dev_C, size_t M, size_t N, size_t K,
                     void *dev_ws, size_t ws_bytes, void *stream);

@@ -595,6 +595,7 @@ icm_status icm_ppmm_workspace_bytes(icm_form form, uint32_t n_limbs, size_t M, s
             if (form != ICM_FORM_I8_DIGITS) *bytes += 256 + crt_scratch_bytes(n_limbs, P, N, M);
             return ICM_OK;
         }
+        case ICM_FORM_I8_P2: *bytes = (size_t)n_limbs * 2 * N * i8_kpad(K); return ICM_OK;
         default: return fail(ICM_EUNSUPPORTED, "form not built");
     }
 }
@@ -609,6 +610,11 @@ icm_status icm_ppmm(icm_form form, const uint64_t *q, uint32_t n_limbs, const ui
         if (q[l] < 3 || q[l] >= (1ull << 60) || !(q[l] & 1)) return fail(ICM_EINVAL, "moduli must be odd and below 2^60");
     if ((uint64_t)K >= (1ull << 32)) return fail(ICM_EBOUND, "K too large for exact accumulation");
     std::vector<uint64_t> qv(q, q + n_limbs);
+    I8Consts kp2;
+    if (form == ICM_FORM_I8_P2) {                       // moduli checked before any device call
+        const char *why = "";
+        if (!make_i8_consts(form, qv.data(), qv.size(), K, kp2, &why)) return fail(ICM_EINVAL, why);
+    }
     const LimbTable lt = make_limb_table(qv);
     if (crt_set_attributes() != cudaSuccess) return fail(ICM_ECUDA, "kernel attributes");
     cudaError_t e;
@@ -623,6 +629,15 @@ icm_status icm_ppmm(icm_form form, const uint64_t *q, uint32_t n_limbs, const ui
             e = launch_planes(form, k, dev_B, (int8_t *)dev_ws, N, K, i8_kpad(K), (cudaStream_t)stream);
             if (e == cudaSuccess)
                 e = launch_ppmm_i8(form, k, dev_A, false, (const int8_t *)dev_ws, dev_C, M, N, K, i8_kpad(K),
+                                   (cudaStream_t)stream);
+            break;
+        }
+        case ICM_FORM_I8_P2: {
+            const size_t pl = (size_t)n_limbs * 2 * N * i8_kpad(K);
+            if (pl && (!dev_ws || ws_bytes < pl)) return fail(ICM_ENOMEM, "workspace too small");
+            e = launch_planes(form, kp2, dev_B, (int8_t *)dev_ws, N, K, i8_kpad(K), (cudaStream_t)stream);
+            if (e == cudaSuccess)
+                e = launch_ppmm_i8(form, kp2, dev_A, false, (const int8_t *)dev_ws, dev_C, M, N, K, i8_kpad(K),
                                    (cudaStream_t)stream);
             break;
         }

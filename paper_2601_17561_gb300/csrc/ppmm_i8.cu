@@ -18,6 +18,15 @@
 // kappa = round(sum_i y_i / m_i) (C / M lies within 2^-8 of zero, so fp32 decides kappa exactly).
 // Residues of the database operand are formed on the fly from its digits with two dp4a.
 //
+// Base-p digit form (the paper's own modulus family, Section 6.2.2: Q = prod p^2): for q = p^2
+// with odd p <= 253 the centred lift x in (-q/2, q/2] splits as x = x0 + p x1 with x0 the centred
+// residue of x mod p (|x0| <= (p-1)/2) and |x1| <= 126, and
+// x y = x0 y0 + p (x0 y1 + x1 y0) (mod p^2).  k_ppmm_p2 sweeps K once: every slab's database
+// words are split into both digit planes in shared memory, and three int8 products per fragment
+// feed two int32 accumulators, T_0 = sum x0 y0 and T_1 = sum (x0 y1 + x1 y0) (the paper's
+// K-concatenation of the two cross products); every chunk of 65,504 columns (2 Kc 2^14 < 2^31)
+// folds (T_0 + p T_1) mod p^2 into the result.
+//
 // Tiling: 128 x 64 output tile per 256-thread block (8 warps, 32 x 32 each, 2 x 4 m16n8 tiles),
 // K in slabs of 32.  Operands are converted into shared memory directly in mma fragment order
 // (one 16-byte load per A fragment, one 8-byte load per B fragment, conflict-free).  The query
@@ -78,6 +87,29 @@ __device__ __forceinline__ int residue_from_digits(uint32_t dlo, uint32_t dhi, i
     const int h = (m - 1) >> 1;
     r = r > h ? r - m : (r < -h ? r + m : r);
     return r;
+}
+
+// Centred base-p digits (x0, x1) of the centred lift of a residue v of q = p^2 (odd p <= 253):
+// x1 = round(x / p) (|x| < 2^15, so the fp32 quotient is exact to far below 1/(2p) and x / p is
+// never a half-integer for odd p), x0 = x - p x1.
+__device__ __forceinline__ void pdigits(uint64_t v, uint64_t q, int pb, float ip, int &x0, int &x1) {
+    const int x = (int)(v > (q >> 1) ? (int64_t)v - (int64_t)q : (int64_t)v);
+    x1 = __float2int_rn((float)x * ip);
+    x0 = x - x1 * pb;
+    const int h = (pb - 1) >> 1;
+    if (x0 > h) { x0 -= pb; ++x1; } else if (x0 < -h) { x0 += pb; --x1; }
+}
+
+// Base-p digits of 4 residues (same row, 4 consecutive k): out[t] packs digit t of the 4 values.
+__device__ __forceinline__ void pdigits4(const uint64_t (&x)[4], uint64_t q, int pb, float ip, uint32_t (&out)[2]) {
+    out[0] = out[1] = 0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        int d0, d1;
+        pdigits(x[e], q, pb, ip, d0, d1);
+        out[0] |= (uint32_t)(d0 & 0xFF) << (8 * e);
+        out[1] |= (uint32_t)(d1 & 0xFF) << (8 * e);
+    }
 }
 
 template <int FORM>
@@ -224,13 +256,129 @@ __global__ void __launch_bounds__(NT, 1) k_ppmm_i8(I8Args p) {
             }
 }
 
+// p^2 form, one sweep over K (see the file comment).  Same 128 x 64 tile and fragment layout as
+// k_ppmm_i8; blockIdx.x enumerates (row tile, column tile) with column tiles fastest so that the
+// blocks in flight share one row tile of the database operand in L2.
+__global__ void __launch_bounds__(NT, 1) k_ppmm_p2(I8Args p) {
+    __shared__ __align__(16) uint32_t sA[2][MT][32][4];
+    __shared__ __align__(16) uint32_t sB[2][NTL][32][2];
+    const uint32_t l = blockIdx.z;
+    const uint64_t M = p.M, N = p.N, K = p.K, Kp = p.Kp;
+    const uint64_t n_tiles = (N + BN - 1) / BN;
+    const uint64_t m0 = (uint64_t)blockIdx.x / n_tiles * BM, n0 = (uint64_t)blockIdx.x % n_tiles * BN;
+    const uint64_t *Al = p.A + (size_t)l * M * K;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp & 3, wn = warp >> 2;
+    const uint64_t q = p.k.q[l], r64 = p.k.r64[l];
+    const int pb = p.k.pd[l];
+    const float ip = p.k.inv_p[l];
+    const int8_t *Bl = p.Bp + (size_t)l * 2 * N * Kp;
+    constexpr uint64_t KC = (2147483647u / (16384u * 2u)) / BK * BK;   // 65,504
+
+    uint32_t R[2][4][4];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) R[a][b][c] = 0;
+
+    for (uint64_t c0 = 0; c0 < K; c0 += KC) {
+        int acc0[2][4][4], acc1[2][4][4];
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) { acc0[a][b][c] = 0; acc1[a][b][c] = 0; }
+        const uint64_t c1 = min(K, c0 + KC);
+        for (uint64_t k0 = c0; k0 < c1; k0 += BK) {
+            __syncthreads();
+            // ---- A: 128 rows x 32 k, split into both digit planes
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int idx = tid + e * NT, r = idx >> 3, g = idx & 7;
+                uint64_t x[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const uint64_t k = k0 + g * 4 + j;
+                    x[j] = (m0 + r < M && k < K) ? __ldg(Al + (m0 + r) * K + k) : 0ull;
+                }
+                const int mt = r >> 4, rr = r & 15;
+                const int reg = (rr >> 3) + ((g >> 2) << 1), ln = ((rr & 7) << 2) + (g & 3);
+                uint32_t d[2];
+                pdigits4(x, q, pb, ip, d);
+                sA[0][mt][ln][reg] = d[0];
+                sA[1][mt][ln][reg] = d[1];
+            }
+            // ---- B: both digit planes, 64 columns x 32 k each
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int8_t *Bu = Bl + (size_t)u * N * Kp;
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int idx = tid + e * NT, cidx = idx >> 3, g = idx & 7;
+                    uint32_t w = 0;
+                    if (n0 + cidx < N) w = __ldg(reinterpret_cast<const uint32_t *>(Bu + (n0 + cidx) * Kp + k0 + g * 4));
+                    sB[u][cidx >> 3][((cidx & 7) << 2) + (g & 3)][g >> 2] = w;
+                }
+            }
+            __syncthreads();
+            // ---- MMA: x0 y0 into acc0, x0 y1 and x1 y0 into acc1
+            uint4 a0[2], a1[2];
+            uint2 b0[4], b1[4];
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                a0[a] = *reinterpret_cast<const uint4 *>(&sA[0][wm * 2 + a][lane][0]);
+                a1[a] = *reinterpret_cast<const uint4 *>(&sA[1][wm * 2 + a][lane][0]);
+            }
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                b0[b] = *reinterpret_cast<const uint2 *>(&sB[0][wn * 4 + b][lane][0]);
+                b1[b] = *reinterpret_cast<const uint2 *>(&sB[1][wn * 4 + b][lane][0]);
+            }
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    mma_s8(acc0[a][b], a0[a], b0[b]);
+                    mma_s8(acc1[a][b], a0[a], b1[b]);
+                    mma_s8(acc1[a][b], a1[a], b0[b]);
+                }
+        }
+        // ---- fold the chunk: R += (T_0 + p T_1) mod p^2 (|T_0 + p T_1| < 2^40, exact in int64)
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int64_t t = (int64_t)acc0[a][b][c] + (int64_t)pb * (int64_t)acc1[a][b][c];
+                    R[a][b][c] = (uint32_t)add_mod(R[a][b][c], reduce_s64(t, q, r64), q);
+                }
+    }
+    // ---- store (column-major output)
+    const int g = lane >> 2, tq = lane & 3;
+    uint64_t *Cl = p.C + (size_t)l * N * M;
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const uint64_t row = m0 + (uint64_t)(wm * 2 + a) * 16 + g + (c >> 1) * 8;
+                const uint64_t col = n0 + (uint64_t)(wn * 4 + b) * 8 + tq * 2 + (c & 1);
+                if (row < M && col < N) Cl[col * M + row] = R[a][b][c];
+            }
+}
+
 // Query planes: for each residue of the extended operand [L][N][K], digit planes (8) or
 // centred residue planes (n_mod) in [L][P][N][Kp], zero padded to Kp.
 template <int FORM>
 __global__ void __launch_bounds__(256) k_planes(const uint64_t *op, int8_t *planes, uint64_t N, uint64_t K,
                                                 uint64_t Kp, icm::I8Consts k) {
     const uint32_t l = blockIdx.y;
-    const int P = FORM == 0 ? 8 : (int)k.n_mod;
+    const int P = FORM == 0 ? 8 : (FORM == 2 ? 2 : (int)k.n_mod);
     const uint64_t q = k.q[l];
     const uint64_t total = N * Kp;
     for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (uint64_t)gridDim.x * blockDim.x) {
@@ -242,6 +390,11 @@ __global__ void __launch_bounds__(256) k_planes(const uint64_t *op, int8_t *plan
         if (FORM == 0) {
 #pragma unroll
             for (int t = 0; t < 8; ++t) dst[(size_t)t * N * Kp] = (int8_t)(((y >> (8 * t)) & 0xFF) ^ 0x80);
+        } else if (FORM == 2) {
+            int d0, d1;
+            pdigits(v, q, k.pd[l], k.inv_p[l], d0, d1);
+            dst[0] = (int8_t)d0;
+            dst[(size_t)N * Kp] = (int8_t)d1;
         } else {
             const uint32_t dlo = (uint32_t)y ^ 0x80808080u, dhi = (uint32_t)(y >> 32) ^ 0x80808080u;
             for (int i = 0; i < P; ++i)
@@ -260,7 +413,8 @@ cudaError_t launch_planes(int form, const I8Consts &k, const uint64_t *op, int8_
     const uint64_t total = N * Kp;
     const unsigned blocks = (unsigned)std::min<uint64_t>((total + 255) / 256, 152u * 32u);
     dim3 grid(blocks, k.n_limbs);
-    k_planes<0><<<grid, 256, 0, st>>>(op, planes, N, K, Kp, k);
+    if (form == ICM_FORM_I8_P2) k_planes<2><<<grid, 256, 0, st>>>(op, planes, N, K, Kp, k);
+    else k_planes<0><<<grid, 256, 0, st>>>(op, planes, N, K, Kp, k);
     return cudaGetLastError();
 }
 
@@ -268,8 +422,15 @@ cudaError_t launch_ppmm_i8(int form, const I8Consts &k, const uint64_t *A, bool 
                            uint64_t M, uint64_t N, uint64_t K, uint64_t Kp, cudaStream_t st) {
     if (M == 0 || N == 0) return cudaSuccess;
     I8Args a{A, Bp, C, M, N, K, Kp, k, a_digits ? 1 : 0};
-    dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((N + BN - 1) / BN), k.n_limbs);
-    k_ppmm_i8<0><<<grid, NT, 0, st>>>(a);
+    if (form == ICM_FORM_I8_P2) {
+        const uint64_t tiles = ((N + BN - 1) / BN) * ((M + BM - 1) / BM);
+        if (tiles > 0x7FFFFFFFull) return cudaErrorInvalidConfiguration;
+        dim3 grid((unsigned)tiles, 1, k.n_limbs);
+        k_ppmm_p2<<<grid, NT, 0, st>>>(a);
+    } else {
+        dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((N + BN - 1) / BN), k.n_limbs);
+        k_ppmm_i8<0><<<grid, NT, 0, st>>>(a);
+    }
     return cudaGetLastError();
 }
 
@@ -319,7 +480,7 @@ uint32_t crt_moduli(const uint64_t *q, size_t nq, uint64_t K, int (&mods)[ICM_MA
 
 uint32_t i8_planes(int form, const uint64_t *q, size_t nq, uint64_t K) {
     int mods[ICM_MAX_MODULI];
-    return form == ICM_FORM_I8_DIGITS ? 8u : crt_moduli(q, nq, K, mods);
+    return form == ICM_FORM_I8_DIGITS ? 8u : form == ICM_FORM_I8_P2 ? 2u : crt_moduli(q, nq, K, mods);
 }
 
 bool make_i8_consts(int form, const uint64_t *q, size_t nq, uint64_t K, I8Consts &k, const char **why) {
@@ -330,6 +491,22 @@ bool make_i8_consts(int form, const uint64_t *q, size_t nq, uint64_t K, I8Consts
         k.q[l] = q[l];
         k.r64[l] = (uint64_t)(((u128)1 << 64) / q[l]);
         for (int s = 0; s < 15; ++s) { k.pw8[l][s] = powmod_h(2, 8ull * s, q[l]); k.pw8s[l][s] = shoup_h(k.pw8[l][s], q[l]); }
+    }
+    if (form == ICM_FORM_I8_P2) {
+        // q = p^2 with odd 3 <= p <= 253: digits fit int8; weights 1 and p of the two passes
+        for (size_t l = 0; l < nq; ++l) {
+            const uint64_t pb = (uint64_t)std::llround(std::sqrt((double)q[l]));
+            if (pb * pb != q[l] || pb < 3 || pb > 253 || !(pb & 1)) {
+                *why = "the p^2 form needs moduli p^2 with odd 3 <= p <= 253";
+                return false;
+            }
+            k.pd[l] = (int32_t)pb;
+            k.inv_p[l] = 1.0f / (float)pb;
+            k.pw8[l][0] = 1; k.pw8s[l][0] = shoup_h(1, q[l]);
+            k.pw8[l][1] = pb; k.pw8s[l][1] = shoup_h(pb, q[l]);
+        }
+        k.n_mod = 0;
+        return true;
     }
     if (form == ICM_FORM_I8_DIGITS) {
         // chunking keeps p * Kc * 2^14 <= 2^31 - 1 for every shift (p <= 8); nothing else to check

@@ -25,12 +25,15 @@ struct I8Consts {
     uint32_t magic[ICM_MAX_MODULI], hneg2[ICM_MAX_MODULI];
     uint64_t W[ICM_MAX_LIMBS][ICM_MAX_MODULI], Ws[ICM_MAX_LIMBS][ICM_MAX_MODULI];
     uint64_t Mq[ICM_MAX_LIMBS], Mqs[ICM_MAX_LIMBS];
+    // p^2 form: q_l = pd_l^2, digit base pd_l and 1 / pd_l (pw8[l][0..1] hold 1 and pd_l)
+    int32_t pd[ICM_MAX_LIMBS];
+    float inv_p[ICM_MAX_LIMBS];
 };
 
 // Builds the constants for primes q and contraction depth K; returns false (with a reason in
 // `why`) if the int32 overflow invariant or the CRT range cannot be met.
 bool make_i8_consts(int form, const uint64_t *q, size_t nq, uint64_t K, I8Consts &out, const char **why);
-// Planes per residue: 8 digit planes or n_mod residue planes.
+// Planes per residue: 8 digit planes, 2 base-p digit planes (p^2 form) or n_mod residue planes.
 uint32_t i8_planes(int form, const uint64_t *q, size_t nq, uint64_t K);
 inline uint64_t i8_kpad(uint64_t K) { return (K + 31) / 32 * 32; }
 

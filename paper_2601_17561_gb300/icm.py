@@ -13,8 +13,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libicm.so")
 
 ICM_OK, ICM_EINVAL, ICM_ENOMEM, ICM_ECUDA, ICM_ETIMEOUT, ICM_EBOUND, ICM_EUNSUPPORTED = range(7)
-ICM_FORM_U64, ICM_FORM_I8_DIGITS, ICM_FORM_I8_CRT, ICM_FORM_F16_CRT = range(4)
-FORMS = {"u64": ICM_FORM_U64, "i8_digits": ICM_FORM_I8_DIGITS, "i8_crt": ICM_FORM_I8_CRT, "f16_crt": ICM_FORM_F16_CRT}
+ICM_FORM_U64, ICM_FORM_I8_DIGITS, ICM_FORM_I8_CRT, ICM_FORM_F16_CRT, ICM_FORM_I8_P2 = range(5)
+FORMS = {"u64": ICM_FORM_U64, "i8_digits": ICM_FORM_I8_DIGITS, "i8_crt": ICM_FORM_I8_CRT, "f16_crt": ICM_FORM_F16_CRT,
+         "i8_p2": ICM_FORM_I8_P2}
 
 
 class IcmError(RuntimeError):

@@ -152,3 +152,24 @@ def test_fold_mc_rejects_bad_arguments(lib, bad):
     with pytest.raises(C.IcmError) as e:
         C.icm_fold_mc(a, odd, None, None, 0)                    # misaligned counts
     assert e.value.status == C.ICM_EINVAL
+
+
+# ----------------------------------------------------------------------------- p^2 form (plain product)
+
+def test_p2_form_workspace_and_moduli(lib):
+    """ICM_FORM_I8_P2 takes moduli p^2 of odd p <= 253 (the paper's Q = prod p^2, Section 6.2.2) and
+    two int8 digit planes of the right operand; other moduli are rejected before any device work."""
+    assert C.icm_ppmm_workspace_bytes(C.ICM_FORM_I8_P2, 3, 100, 37, 1000) == 3 * 2 * 37 * 1024
+    for bad in ([127 * 127 + 2], [255 * 255], [1], [127 * 127, 35], [2 * 2], [254 * 254]):
+        with pytest.raises(C.IcmError) as e:
+            C.icm_ppmm(C.ICM_FORM_I8_P2, bad, len(bad), None, None, None, 0, 0, 0, stream=0)
+        assert e.value.status == C.ICM_EINVAL, bad
+
+
+def test_paper_p2_modulus():
+    """Section 6.2.2: Q = prod of p^2 over the primes 127 <= p <= 253 gives 24 moduli, 48 int8
+    matrices per operand, and about 2^357 (the paper's target; the product is 2^360.8)."""
+    ps = [p for p in range(127, 254) if all(p % d for d in range(2, int(p ** 0.5) + 1))]
+    assert len(ps) == 24 and 2 * len(ps) == 48
+    bits = sum(2 * np.log2(p) for p in ps)
+    assert 357 <= bits < 362
