@@ -283,79 +283,94 @@ __global__ void __launch_bounds__(NT, 1) k_ppmm_p2(I8Args p) {
 #pragma unroll
             for (int c = 0; c < 4; ++c) R[a][b][c] = 0;
 
-    for (uint64_t c0 = 0; c0 < K; c0 += KC) {
-        int acc0[2][4][4], acc1[2][4][4];
+    // the next slab's words are loaded into registers while the current one is multiplied
+    uint64_t xr[4][4];
+    uint32_t br[2][2];
+    auto load = [&](uint64_t k0) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int idx = tid + e * NT, r = idx >> 3, g = idx & 7;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint64_t k = k0 + g * 4 + j;
+                xr[e][j] = (m0 + r < M && k < K) ? __ldg(Al + (m0 + r) * K + k) : 0ull;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int idx = tid + e * NT, cidx = idx >> 3, g = idx & 7;
+                br[u][e] = n0 + cidx < N
+                    ? __ldg(reinterpret_cast<const uint32_t *>(Bl + (size_t)u * N * Kp + (n0 + cidx) * Kp + k0 + g * 4))
+                    : 0u;
+            }
+    };
+    int acc0[2][4][4], acc1[2][4][4];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) { acc0[a][b][c] = 0; acc1[a][b][c] = 0; }
+    if (K > 0) load(0);
+    for (uint64_t k0 = 0; k0 < K; k0 += BK) {
+        __syncthreads();
+        // ---- A: 128 rows x 32 k split into both digit planes; B: both planes, 64 columns x 32 k
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int idx = tid + e * NT, r = idx >> 3, g = idx & 7;
+            const int mt = r >> 4, rr = r & 15;
+            const int reg = (rr >> 3) + ((g >> 2) << 1), ln = ((rr & 7) << 2) + (g & 3);
+            uint32_t d[2];
+            pdigits4(xr[e], q, pb, ip, d);
+            sA[0][mt][ln][reg] = d[0];
+            sA[1][mt][ln][reg] = d[1];
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int idx = tid + e * NT, cidx = idx >> 3, g = idx & 7;
+                sB[u][cidx >> 3][((cidx & 7) << 2) + (g & 3)][g >> 2] = br[u][e];
+            }
+        __syncthreads();
+        if (k0 + BK < K) load(k0 + BK);
+        // ---- MMA: x0 y0 into acc0, x0 y1 and x1 y0 into acc1
+        uint4 a0[2], a1[2];
+        uint2 b0[4], b1[4];
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            a0[a] = *reinterpret_cast<const uint4 *>(&sA[0][wm * 2 + a][lane][0]);
+            a1[a] = *reinterpret_cast<const uint4 *>(&sA[1][wm * 2 + a][lane][0]);
+        }
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            b0[b] = *reinterpret_cast<const uint2 *>(&sB[0][wn * 4 + b][lane][0]);
+            b1[b] = *reinterpret_cast<const uint2 *>(&sB[1][wn * 4 + b][lane][0]);
+        }
 #pragma unroll
         for (int a = 0; a < 2; ++a)
 #pragma unroll
-            for (int b = 0; b < 4; ++b)
-#pragma unroll
-                for (int c = 0; c < 4; ++c) { acc0[a][b][c] = 0; acc1[a][b][c] = 0; }
-        const uint64_t c1 = min(K, c0 + KC);
-        for (uint64_t k0 = c0; k0 < c1; k0 += BK) {
-            __syncthreads();
-            // ---- A: 128 rows x 32 k, split into both digit planes
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int idx = tid + e * NT, r = idx >> 3, g = idx & 7;
-                uint64_t x[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const uint64_t k = k0 + g * 4 + j;
-                    x[j] = (m0 + r < M && k < K) ? __ldg(Al + (m0 + r) * K + k) : 0ull;
-                }
-                const int mt = r >> 4, rr = r & 15;
-                const int reg = (rr >> 3) + ((g >> 2) << 1), ln = ((rr & 7) << 2) + (g & 3);
-                uint32_t d[2];
-                pdigits4(x, q, pb, ip, d);
-                sA[0][mt][ln][reg] = d[0];
-                sA[1][mt][ln][reg] = d[1];
-            }
-            // ---- B: both digit planes, 64 columns x 32 k each
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int8_t *Bu = Bl + (size_t)u * N * Kp;
-#pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    const int idx = tid + e * NT, cidx = idx >> 3, g = idx & 7;
-                    uint32_t w = 0;
-                    if (n0 + cidx < N) w = __ldg(reinterpret_cast<const uint32_t *>(Bu + (n0 + cidx) * Kp + k0 + g * 4));
-                    sB[u][cidx >> 3][((cidx & 7) << 2) + (g & 3)][g >> 2] = w;
-                }
-            }
-            __syncthreads();
-            // ---- MMA: x0 y0 into acc0, x0 y1 and x1 y0 into acc1
-            uint4 a0[2], a1[2];
-            uint2 b0[4], b1[4];
-#pragma unroll
-            for (int a = 0; a < 2; ++a) {
-                a0[a] = *reinterpret_cast<const uint4 *>(&sA[0][wm * 2 + a][lane][0]);
-                a1[a] = *reinterpret_cast<const uint4 *>(&sA[1][wm * 2 + a][lane][0]);
-            }
-#pragma unroll
             for (int b = 0; b < 4; ++b) {
-                b0[b] = *reinterpret_cast<const uint2 *>(&sB[0][wn * 4 + b][lane][0]);
-                b1[b] = *reinterpret_cast<const uint2 *>(&sB[1][wn * 4 + b][lane][0]);
+                mma_s8(acc0[a][b], a0[a], b0[b]);
+                mma_s8(acc1[a][b], a0[a], b1[b]);
+                mma_s8(acc1[a][b], a1[a], b0[b]);
             }
+        // ---- end of a chunk of KC columns (or of K): R += (T_0 + p T_1) mod p^2, exact in int64
+        if ((k0 + BK) % KC == 0 || k0 + BK >= K) {
 #pragma unroll
             for (int a = 0; a < 2; ++a)
 #pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    mma_s8(acc0[a][b], a0[a], b0[b]);
-                    mma_s8(acc1[a][b], a0[a], b1[b]);
-                    mma_s8(acc1[a][b], a1[a], b0[b]);
-                }
+                for (int b = 0; b < 4; ++b)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const int64_t t = (int64_t)acc0[a][b][c] + (int64_t)pb * (int64_t)acc1[a][b][c];
+                        R[a][b][c] = (uint32_t)add_mod(R[a][b][c], reduce_s64(t, q, r64), q);
+                        acc0[a][b][c] = 0;
+                        acc1[a][b][c] = 0;
+                    }
         }
-        // ---- fold the chunk: R += (T_0 + p T_1) mod p^2 (|T_0 + p T_1| < 2^40, exact in int64)
-#pragma unroll
-        for (int a = 0; a < 2; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b)
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const int64_t t = (int64_t)acc0[a][b][c] + (int64_t)pb * (int64_t)acc1[a][b][c];
-                    R[a][b][c] = (uint32_t)add_mod(R[a][b][c], reduce_s64(t, q, r64), q);
-                }
     }
     // ---- store (column-major output)
     const int g = lane >> 2, tq = lane & 3;
