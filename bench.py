@@ -518,22 +518,24 @@ def main():
     fd = None
     if args.fold_trials > 0:
         from paper_2601_17561_gb300 import folding as FD
+        # weak scaling: every rank runs fold_trials trials of one run, its own consecutive range
+        t0, n_local = shard.trial_range(rank, ws, ws * args.fold_trials)
         with torch.cuda.stream(st):
             r = FD.fold_mc(1 << 26, seed=1, stream=st)                   # warm-up
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(st)
-            FD.fold_mc(args.fold_trials, seed=2, trial0=0, out=r, stream=st)
+            FD.fold_mc(n_local, seed=2, trial0=t0, out=r, stream=st)
             b.record(st)
             st.synchronize()
-        fms = a.elapsed_time(b)
-        rate = args.fold_trials / (fms / 1e3)
+        fms = shard.job_time_ms(a.elapsed_time(b), dist, dev)
+        rate = ws * args.fold_trials / (fms / 1e3)
         imadw = 8 * 10 * 2 * 4                                           # 32x32->64 partial products per trial
         ipeak = C.icm_probe_peak(0)
-        fd = {"kernel": "k_fold_mc<7>", "trials": args.fold_trials, "ms": fms, "trials_per_s": rate,
-              "counts": [int(x) for x in r.counts.cpu()], "k": FD.FOLD_K, "n_f": FD.N_F, "p_f": FD.P_F,
-              "law": FD.NEG_LAW, "positive_interval": (0.3, 0.45),
-              "roofline": {"bound": "alu", "achieved": imadw * rate / 1e9, "peak": ipeak / 1e9, "unit": "Gop/s",
-                           "frac": imadw * rate / ipeak,
+        fd = {"kernel": "k_fold_mc<7>", "trials": ws * args.fold_trials, "ms": fms, "trials_per_s": rate,
+              "counts": [int(x) for x in shard.job_sum(r.counts, dist).cpu()], "k": FD.FOLD_K, "n_f": FD.N_F,
+              "p_f": FD.P_F, "law": FD.NEG_LAW, "positive_interval": (0.3, 0.45),
+              "roofline": {"bound": "alu", "achieved": imadw * rate / ws / 1e9, "peak": ipeak / 1e9, "unit": "Gop/s",
+                           "frac": imadw * rate / ws / ipeak,
                            "peak_source": "measured in this run: IMAD.WIDE issue-bound probe (icm_probe_peak 0)",
                            "ops": "Philox 64x64->128 products as 4 IMAD.WIDE each, 640 per trial"}}
         del r

@@ -6,6 +6,9 @@ encrypted database shard -- its own MSRLWE database, whose a-part stream is keye
 and every rank matches the same query batch.  The job's rate is all ranks' comparisons over the
 slowest rank's time.  (A deployment would all-gather the query operand once per batch; here every
 rank encrypts the same seeded batch.)
+
+The cleartext folding check shards by trial: Philox counters are keyed by the trial index, so
+consecutive trial ranges on the ranks are together exactly the single run's trials.
 """
 from __future__ import annotations
 
@@ -40,3 +43,19 @@ def job_time_ms(local_ms: float, dist=None, device=None) -> float:
 def job_rate(world: int, comparisons_per_rank: int, job_ms: float) -> float:
     """Whole-job comparisons per second (weak scaling: every rank processes its own shard)."""
     return world * comparisons_per_rank / (job_ms / 1e3)
+
+
+def trial_range(rank: int, world: int, n_trials: int) -> tuple[int, int]:
+    """(first trial, number of trials) of rank's share of a run of n_trials trials: consecutive
+    ranges, the first n_trials % world ranks one trial longer."""
+    base, extra = divmod(int(n_trials), int(world))
+    return rank * base + min(rank, extra), base + (1 if rank < extra else 0)
+
+
+def job_sum(t: torch.Tensor, dist=None) -> torch.Tensor:
+    """Counters summed over the ranks (all-reduce SUM when a process group of more than one rank
+    is initialised), for reporting."""
+    t = t.clone()
+    if dist is not None and dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return t

@@ -79,3 +79,51 @@ def test_two_ranks_shard_the_database():
     # the job time is the slowest rank's; the rate counts every rank's comparisons
     assert t == 10.0 * WORLD
     assert shard.job_rate(WORLD, N_EYES * N_DB, t) == WORLD * N_EYES * N_DB / (t / 1e3)
+
+
+def _fold_rank_main(rank, world, port, n, out_q):
+    """One rank of a sharded folding check: its consecutive trial range, counters summed."""
+    import torch
+    from oracle import folding as F
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        t0, cnt = shard.trial_range(rank, world, n)
+        fmin, fmax = F.poly_range(F.PAPER_FOLD_COEF, 0.3, 0.3005)
+        r = F.fold_mc(F.PAPER_FOLD_COEF, *F.PAPER_D, 16, (0.3, 0.3005), (0.0, 0.03), (fmin + 0.01, fmin + 0.02),
+                      seed=21, trial0=t0, n_trials=cnt, hist=(-0.02, 0.08, 20))
+        counts = shard.job_sum(torch.from_numpy(r["counts"]), dist).numpy()
+        hist = shard.job_sum(torch.from_numpy(r["hist"]), dist).numpy()
+        sums = [None] * world
+        dist.all_gather_object(sums, (t0, cnt, r["sk"], r["sk1"]))
+        if rank == 0:
+            out_q.put((counts, hist, sums))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_ranks_shard_the_folding_trials():
+    """The folding check's N > 1 path: each rank runs its own consecutive trial range (an odd total,
+    so the ranges differ in length); the summed counters and histograms, and the ranks' per-trial
+    sums in rank order, equal the single run's."""
+    from oracle import folding as F
+    n = 6001
+    ctx = mp.get_context("spawn")
+    out_q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_fold_rank_main, args=(r, WORLD, port, n, out_q)) for r in range(WORLD)]
+    for p in procs:
+        p.start()
+    counts, hist, sums = out_q.get(timeout=300)
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    assert [(s[0], s[1]) for s in sums] == [(0, 3001), (3001, 3000)]
+    fmin, fmax = F.poly_range(F.PAPER_FOLD_COEF, 0.3, 0.3005)
+    one = F.fold_mc(F.PAPER_FOLD_COEF, *F.PAPER_D, 16, (0.3, 0.3005), (0.0, 0.03), (fmin + 0.01, fmin + 0.02),
+                    seed=21, trial0=0, n_trials=n, hist=(-0.02, 0.08, 20))
+    assert np.array_equal(counts, one["counts"]) and np.array_equal(hist, one["hist"])
+    assert np.array_equal(np.concatenate([s[2] for s in sums]), one["sk"])
+    assert np.array_equal(np.concatenate([s[3] for s in sums]), one["sk1"])
+    assert shard.trial_range(3, 4, 10) == (8, 2) and shard.trial_range(0, 4, 10) == (0, 3)
