@@ -483,7 +483,7 @@ def main():
                     "peak_source": "measured in this run: int8 mma.sync.m16n8k32 issue-bound probe (no tcgen05 int8 on sm_103a)"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = NCU_TRAFFIC.get((args.form, tune["chosen"] if tc else 0))
-    roof["kernel"] = {"u64": "k_ppmm_u64", "i8_digits": "k_ppmm_i8<0>", "i8_crt": "k_crt_p1<int8> + k_crt_combine",
+    roof["kernel"] = {"u64": "k_ppmm_u64", "i8_digits": "k_ppmm_digits", "i8_crt": "k_crt_p1<int8> + k_crt_combine",
                       "f16_crt": f"k_crt_tc ({C.VARIANTS[tune['chosen']]}) + k_crt_combine" if tc
                       else "k_crt_p1<fp16> + k_crt_combine"
                       }.get(args.form)

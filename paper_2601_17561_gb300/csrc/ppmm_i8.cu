@@ -27,10 +27,13 @@
 // K-concatenation of the two cross products); every chunk of 65,504 columns (2 Kc 2^14 < 2^31)
 // folds (T_0 + p T_1) mod p^2 into the result.
 //
-// Tiling: 128 x 64 output tile per 256-thread block (8 warps, 32 x 32 each, 2 x 4 m16n8 tiles),
-// K in slabs of 32.  Operands are converted into shared memory directly in mma fragment order
-// (one 16-byte load per A fragment, one 8-byte load per B fragment, conflict-free).  The query
-// operand comes pre-split into int8 planes [L][P][N][Kp] (Kp: K rounded up to 32, zero padded).
+// Tiling (k_ppmm_digits, k_ppmm_p2): 128 x 64 output tile per 256-thread block (8 warps, 32 x 32
+// each, 2 x 4 m16n8 tiles), K in slabs of 32; the next slab's words are loaded into registers while
+// the current one is multiplied.  Operands are converted into shared memory directly in mma
+// fragment order (one 16-byte load per A fragment, one 8-byte load per B fragment,
+// conflict-free).  The query operand comes pre-split into int8 planes [L][P][N][Kp] (Kp: K rounded
+// up to 32, zero padded).  This file builds the CRT form's constants and query planes; its
+// products run in ppmm_crt.cu (k_crt_p1) and ppmm_crt_tc.cu (k_crt_tc).
 #include "icm_internal.h"
 #include "ppmm_i8.h"
 
@@ -112,10 +115,17 @@ __device__ __forceinline__ void pdigits4(const uint64_t (&x)[4], uint64_t q, int
     }
 }
 
-template <int FORM>
-__global__ void __launch_bounds__(NT, 1) k_ppmm_i8(I8Args p) {
-    __shared__ __align__(16) uint32_t sA[8][MT][32][4];
-    __shared__ __align__(16) uint32_t sB[8][NTL][32][2];
+// Digit form: one pass per shift s = 0..14 over the pairs t + u = s.  The next slab's database
+// words and query plane words are loaded into registers while the current slab is multiplied; the
+// modular results R (32 u64 per thread, updated once per K-chunk) live in shared memory to leave
+// the registers to the prefetch.  Dynamic shared memory: sA 32 KB, sB 16 KB, sR 64 KB.
+constexpr size_t DIG_SMEM = 8 * MT * 32 * 4 * 4 + 8 * NTL * 32 * 2 * 4 + 32 * NT * 8;
+
+__global__ void __launch_bounds__(NT, 1) k_ppmm_digits(I8Args p) {
+    extern __shared__ __align__(16) uint8_t dsm[];
+    uint32_t (*sA)[MT][32][4] = reinterpret_cast<uint32_t (*)[MT][32][4]>(dsm);
+    uint32_t (*sB)[NTL][32][2] = reinterpret_cast<uint32_t (*)[NTL][32][2]>(dsm + 8 * MT * 32 * 4 * 4);
+    uint64_t *sR = reinterpret_cast<uint64_t *>(dsm + 8 * MT * 32 * 4 * 4 + 8 * NTL * 32 * 2 * 4);   // [32][NT]
     const uint32_t l = blockIdx.z;
     const uint64_t m0 = (uint64_t)blockIdx.x * BM, n0 = (uint64_t)blockIdx.y * BN;
     const uint64_t M = p.M, N = p.N, K = p.K, Kp = p.Kp;
@@ -123,116 +133,97 @@ __global__ void __launch_bounds__(NT, 1) k_ppmm_i8(I8Args p) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int wm = warp & 3, wn = warp >> 2;
     const uint64_t q = p.k.q[l], r64 = p.k.r64[l];
-    const int P = FORM == 0 ? 8 : (int)p.k.n_mod;
-    const int8_t *Bl = p.Bp + (size_t)l * P * N * Kp;
+    const int8_t *Bl = p.Bp + (size_t)l * 8 * N * Kp;
+    for (int i = 0; i < 32; ++i) sR[i * NT + tid] = 0;
 
-    uint64_t R[2][4][4];                      // digit form: modular result; CRT form: sum y_i W_i mod q
-    float F[2][4][4];                         // CRT form: sum y_i / m_i
+    uint64_t xr[4][4];
+    uint32_t br[8][2];
+    for (int pass = 0; pass < 15; ++pass) {
+        const int t_lo = max(0, pass - 7), t_hi = min(7, pass);
+        // K-chunk keeping np * Kc * 2^14 <= 2^31 - 1 for the np pairs of this shift
+        const uint64_t kc = (uint64_t)((2147483647u / (16384u * (uint32_t)(t_hi - t_lo + 1))) / BK * BK);
+        auto load = [&](uint64_t k0) {
 #pragma unroll
-    for (int a = 0; a < 2; ++a)
+            for (int e = 0; e < 4; ++e) {
+                const int idx = tid + e * NT, r = idx >> 3, g = idx & 7;
 #pragma unroll
-        for (int b = 0; b < 4; ++b)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) { R[a][b][c] = 0; F[a][b][c] = 0.f; }
-
-    const int n_pass = FORM == 0 ? 15 : (int)p.k.n_mod;
-    for (int pass = 0; pass < n_pass; ++pass) {
-        const int t_lo = FORM == 0 ? max(0, pass - 7) : 0;
-        const int t_hi = FORM == 0 ? min(7, pass) : 0;
-        const int np = t_hi - t_lo + 1;
-        // K-chunk keeping np * Kc * 2^14 <= 2^31 - 1 (digit form); the CRT form needs one chunk
-        const uint64_t kc = FORM == 0 ? (uint64_t)((2147483647u / (16384u * (uint32_t)np)) / BK * BK) : K + BK;
-        for (uint64_t c0 = 0; c0 < K; c0 += kc) {
-            int acc[2][4][4];
-#pragma unroll
-            for (int a = 0; a < 2; ++a)
-#pragma unroll
-                for (int b = 0; b < 4; ++b)
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) acc[a][b][c] = 0;
-            const uint64_t c1 = min(K, c0 + kc);
-            for (uint64_t k0 = c0; k0 < c1; k0 += BK) {
-                __syncthreads();
-                // ---- A: 128 rows x 32 k, four groups of 4 consecutive k per thread
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int idx = tid + e * NT, r = idx >> 3, g = idx & 7;
-                    uint64_t x[4];
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const uint64_t k = k0 + g * 4 + j;
-                        x[j] = (m0 + r < M && k < K) ? __ldg(Al + (m0 + r) * K + k) : 0ull;
-                    }
-                    const int mt = r >> 4, rr = r & 15;
-                    const int reg = (rr >> 3) + ((g >> 2) << 1), ln = ((rr & 7) << 2) + (g & 3);
-                    if (FORM == 0) {
-                        uint32_t d[8];
-                        digits4(x, q, p.a_digits != 0, d);
-                        for (int t = t_lo; t <= t_hi; ++t) sA[t][mt][ln][reg] = d[t];
-                    } else {
-                        const int m = p.k.mod[pass];
-                        const int wlo = p.k.wlo[pass], whi = p.k.whi[pass];
-                        const float im = p.k.inv_m[pass];
-                        uint32_t word = 0;
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            const uint64_t v = x[j];
-                            const uint64_t y = ((v > (q >> 1)) ? v - q : v) + 0x8080808080808080ull;
-                            const int res = residue_from_digits((uint32_t)y ^ 0x80808080u, (uint32_t)(y >> 32) ^ 0x80808080u,
-                                                                wlo, whi, m, im);
-                            word |= ((uint32_t)(res & 0xFF)) << (8 * j);
-                        }
-                        sA[0][mt][ln][reg] = word;
-                    }
-                }
-                // ---- B planes: 64 columns x 32 k per plane, two words per thread
-                for (int t = t_lo; t <= t_hi; ++t) {
-                    const int u = FORM == 0 ? pass - t : pass;
-                    const int8_t *Bu = Bl + (size_t)u * N * Kp;
-#pragma unroll
-                    for (int e = 0; e < 2; ++e) {
-                        const int idx = tid + e * NT, cidx = idx >> 3, g = idx & 7;
-                        uint32_t w = 0;
-                        if (n0 + cidx < N) w = __ldg(reinterpret_cast<const uint32_t *>(Bu + (n0 + cidx) * Kp + k0 + g * 4));
-                        const int nt = cidx >> 3;
-                        sB[FORM == 0 ? t : 0][nt][((cidx & 7) << 2) + (g & 3)][g >> 2] = w;
-                    }
-                }
-                __syncthreads();
-                // ---- MMA: all pairs of this pass
-                for (int t = t_lo; t <= t_hi; ++t) {
-                    const int ta = FORM == 0 ? t : 0;
-                    uint4 af[2];
-                    uint2 bf[4];
-#pragma unroll
-                    for (int a = 0; a < 2; ++a) af[a] = *reinterpret_cast<const uint4 *>(&sA[ta][wm * 2 + a][lane][0]);
-#pragma unroll
-                    for (int b = 0; b < 4; ++b) bf[b] = *reinterpret_cast<const uint2 *>(&sB[ta][wn * 4 + b][lane][0]);
-#pragma unroll
-                    for (int a = 0; a < 2; ++a)
-#pragma unroll
-                        for (int b = 0; b < 4; ++b) mma_s8(acc[a][b], af[a], bf[b]);
+                for (int j = 0; j < 4; ++j) {
+                    const uint64_t k = k0 + g * 4 + j;
+                    xr[e][j] = (m0 + r < M && k < K) ? __ldg(Al + (m0 + r) * K + k) : 0ull;
                 }
             }
-            // ---- fold the chunk's accumulator into the modular result
 #pragma unroll
-            for (int a = 0; a < 2; ++a)
+            for (int t = 0; t < 8; ++t) {
+                if (t < t_lo || t > t_hi) continue;
+                const int8_t *Bu = Bl + (size_t)(pass - t) * N * Kp;
 #pragma unroll
-                for (int b = 0; b < 4; ++b)
+                for (int e = 0; e < 2; ++e) {
+                    const int idx = tid + e * NT, cidx = idx >> 3, g = idx & 7;
+                    br[t][e] = n0 + cidx < N ? __ldg(reinterpret_cast<const uint32_t *>(Bu + (n0 + cidx) * Kp + k0 + g * 4))
+                                             : 0u;
+                }
+            }
+        };
+        int acc[2][4][4];
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        if (FORM == 0) {
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[a][b][c] = 0;
+        if (K > 0) load(0);
+        for (uint64_t k0 = 0; k0 < K; k0 += BK) {
+            __syncthreads();
+            // ---- A: 128 rows x 32 k into the digit planes of this shift; B: the matching planes
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int idx = tid + e * NT, r = idx >> 3, g = idx & 7;
+                const int mt = r >> 4, rr = r & 15;
+                const int reg = (rr >> 3) + ((g >> 2) << 1), ln = ((rr & 7) << 2) + (g & 3);
+                uint32_t d[8];
+                digits4(xr[e], q, p.a_digits != 0, d);
+#pragma unroll
+                for (int t = 0; t < 8; ++t)
+                    if (t >= t_lo && t <= t_hi) sA[t][mt][ln][reg] = d[t];
+            }
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                if (t < t_lo || t > t_hi) continue;
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int idx = tid + e * NT, cidx = idx >> 3, g = idx & 7;
+                    sB[t][cidx >> 3][((cidx & 7) << 2) + (g & 3)][g >> 2] = br[t][e];
+                }
+            }
+            __syncthreads();
+            if (k0 + BK < K) load(k0 + BK);
+            // ---- MMA: all pairs of this shift
+            for (int t = t_lo; t <= t_hi; ++t) {
+                uint4 af[2];
+                uint2 bf[4];
+#pragma unroll
+                for (int a = 0; a < 2; ++a) af[a] = *reinterpret_cast<const uint4 *>(&sA[t][wm * 2 + a][lane][0]);
+#pragma unroll
+                for (int b = 0; b < 4; ++b) bf[b] = *reinterpret_cast<const uint2 *>(&sB[t][wn * 4 + b][lane][0]);
+#pragma unroll
+                for (int a = 0; a < 2; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) mma_s8(acc[a][b], af[a], bf[b]);
+            }
+            // ---- end of a K-chunk: R += (T_s mod q) (2^(8 s) mod q)
+            if ((k0 + BK) % kc == 0 || k0 + BK >= K) {
+#pragma unroll
+                for (int a = 0; a < 2; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b)
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
                             const uint64_t v = reduce_s64((int64_t)acc[a][b][c], q, r64);
-                            R[a][b][c] = add_mod(R[a][b][c], mulmod_shoup(v, p.k.pw8[l][pass], p.k.pw8s[l][pass], q), q);
-                        } else {
-                            const int m = p.k.mod[pass];
-                            int ci = acc[a][b][c] % m;
-                            ci = ci < 0 ? ci + m : ci;                                        // C mod m_i
-                            const int y = (int)(((uint32_t)ci * (uint32_t)p.k.yinv[pass]) % (uint32_t)m);
-                            R[a][b][c] = add_mod(R[a][b][c], mulmod_shoup((uint64_t)y, p.k.W[l][pass], p.k.Ws[l][pass], q), q);
-                            F[a][b][c] += (float)y * p.k.inv_m[pass];
+                            uint64_t &R = sR[((a * 4 + b) * 4 + c) * NT + tid];
+                            R = add_mod(R, mulmod_shoup(v, p.k.pw8[l][pass], p.k.pw8s[l][pass], q), q);
+                            acc[a][b][c] = 0;
                         }
-                    }
+            }
         }
     }
     // ---- store (column-major output)
@@ -246,18 +237,12 @@ __global__ void __launch_bounds__(NT, 1) k_ppmm_i8(I8Args p) {
             for (int c = 0; c < 4; ++c) {
                 const uint64_t row = m0 + (uint64_t)(wm * 2 + a) * 16 + g + (c >> 1) * 8;
                 const uint64_t col = n0 + (uint64_t)(wn * 4 + b) * 8 + tq * 2 + (c & 1);
-                if (row >= M || col >= N) continue;
-                uint64_t v = R[a][b][c];
-                if (FORM == 1) {
-                    const uint64_t kappa = (uint64_t)__float2int_rn(F[a][b][c]);
-                    v = sub_mod(v, mulmod_shoup(kappa, p.k.Mq[l], p.k.Mqs[l], q), q);
-                }
-                Cl[col * M + row] = v;
+                if (row < M && col < N) Cl[col * M + row] = sR[((a * 4 + b) * 4 + c) * NT + tid];
             }
 }
 
 // p^2 form, one sweep over K (see the file comment).  Same 128 x 64 tile and fragment layout as
-// k_ppmm_i8; blockIdx.x enumerates (row tile, column tile) with column tiles fastest so that the
+// k_ppmm_digits; blockIdx.x enumerates (row tile, column tile) with column tiles fastest so that the
 // blocks in flight share one row tile of the database operand in L2.
 __global__ void __launch_bounds__(NT, 1) k_ppmm_p2(I8Args p) {
     __shared__ __align__(16) uint32_t sA[2][MT][32][4];
@@ -443,8 +428,11 @@ cudaError_t launch_ppmm_i8(int form, const I8Consts &k, const uint64_t *A, bool 
         dim3 grid((unsigned)tiles, 1, k.n_limbs);
         k_ppmm_p2<<<grid, NT, 0, st>>>(a);
     } else {
+        const cudaError_t attr =                         // per device: set at every launch
+            cudaFuncSetAttribute(k_ppmm_digits, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DIG_SMEM);
+        if (attr != cudaSuccess) return attr;
         dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((N + BN - 1) / BN), k.n_limbs);
-        k_ppmm_i8<0><<<grid, NT, 0, st>>>(a);
+        k_ppmm_digits<<<grid, NT, DIG_SMEM, st>>>(a);
     }
     return cudaGetLastError();
 }
