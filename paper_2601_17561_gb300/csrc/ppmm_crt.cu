@@ -285,31 +285,37 @@ __global__ void __launch_bounds__(256) k_crt_combine(P2Args p) {
     if (idx >= cnt) return;
     const uint64_t col = idx / Mall, grow0 = idx % Mall;
     const uint8_t *Rl = p.R + (size_t)l * r * cnt + idx;
-    uint64_t S[V];
+    // sum_i y_i W_i unreduced, over the 32-bit halves of W_i (y_i < 2^8, W_i < 2^60: each half-sum
+    // stays below r 2^40), reduced once at the end; F = sum_i y_i / m_i in fp32 (within 2^-9 of
+    // the integer kappa, so the rounding decides it exactly)
+    uint64_t Alo[V], Ahi[V];
     float F[V];
 #pragma unroll
-    for (int e = 0; e < V; ++e) { S[e] = 0; F[e] = 0.f; }
+    for (int e = 0; e < V; ++e) { Alo[e] = 0; Ahi[e] = 0; F[e] = 0.f; }
     for (uint32_t i = 0; i < r; ++i) {
         const uint32_t w = V == 4 ? *reinterpret_cast<const uint32_t *>(Rl + (size_t)i * cnt) : Rl[(size_t)i * cnt];
         const uint32_t yinv = (uint32_t)p.k.yinv[i], m = (uint32_t)p.k.mod[i], magic = p.k.magic[i];
-        const uint64_t W = p.k.W[l][i], Ws = p.k.Ws[l][i];
+        const uint32_t wlo = (uint32_t)p.k.W[l][i], whi = (uint32_t)(p.k.W[l][i] >> 32);
         const float inv_m = p.k.inv_m[i];
 #pragma unroll
         for (int e = 0; e < V; ++e) {
             const uint32_t x = ((w >> (8 * e)) & 0xFF) * yinv;
             const uint32_t y = x - __umulhi(x, magic) * m;
-            S[e] = add_mod(S[e], mulmod_shoup(y, W, Ws, q), q);
-            F[e] += (float)y * inv_m;
+            Alo[e] += (uint64_t)y * wlo;
+            Ahi[e] += (uint64_t)y * whi;
+            F[e] += (__int_as_float(0x4B000000u | y) - 8388608.f) * inv_m;     // (float)y, exact for y < 2^23
         }
     }
+    const uint64_t r64 = p.k.r64[l], p32 = p.k.pw8[l][4], p32s = p.k.pw8s[l][4];       // 2^32 mod q
 #pragma unroll
     for (int e = 0; e < V; ++e) {
         const uint64_t grow = grow0 + e;
         uint32_t c = 0;
         while (c + 1 < p.tab.n && grow >= p.tab.row0[c + 1]) ++c;
         const uint64_t row = grow - p.tab.row0[c], M = p.tab.M[c];
+        const uint64_t S = add_mod(reduce64(Alo[e], q, r64), mulmod_shoup(reduce64(Ahi[e], q, r64), p32, p32s, q), q);
         const uint64_t kappa = (uint64_t)__float2int_rn(F[e]);
-        p.tab.C[c][((size_t)l * p.N + p.n0 + col) * M + row] = sub_mod(S[e], mulmod_shoup(kappa, p.k.Mq[l], p.k.Mqs[l], q), q);
+        p.tab.C[c][((size_t)l * p.N + p.n0 + col) * M + row] = sub_mod(S, mulmod_shoup(kappa, p.k.Mq[l], p.k.Mqs[l], q), q);
     }
 }
 
