@@ -173,3 +173,24 @@ def test_paper_p2_modulus():
     assert len(ps) == 24 and 2 * len(ps) == 48
     bits = sum(2 * np.log2(p) for p in ps)
     assert 357 <= bits < 362
+
+
+def test_p2_digit_split_exhaustive():
+    """The p^2 form's digit split, as the kernels compute it (x1 = round(x * fl(1/p)) in fp32, x0 =
+    x - p x1, one correction step): for every odd p <= 253 and every residue of p^2, |x0| <= (p-1)/2,
+    |x1| <= 126 (int8 operands) and x0 + p x1 is the centred lift x."""
+    worst = 0
+    for p in range(3, 254, 2):
+        q = p * p
+        v = np.arange(q, dtype=np.int64)
+        x = np.where(v > q // 2, v - q, v)
+        ip = np.float32(1.0) / np.float32(p)
+        x1 = np.rint(x.astype(np.float32) * ip).astype(np.int64)
+        x0 = x - x1 * p
+        h = (p - 1) // 2
+        hi, lo = x0 > h, x0 < -h
+        x0 = np.where(hi, x0 - p, np.where(lo, x0 + p, x0))
+        x1 = np.where(hi, x1 + 1, np.where(lo, x1 - 1, x1))
+        assert np.all(np.abs(x0) <= h) and np.all(x0 + p * x1 == x), p
+        worst = max(worst, int(np.abs(x1).max()))
+    assert worst == 126
