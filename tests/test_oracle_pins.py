@@ -294,6 +294,26 @@ def test_ppmm_bigint_and_extremes():
     assert np.array_equal(O.ppmm(q, I, B)[0], B[0])
 
 
+def test_ppmm_composite_square_moduli():
+    """The same product modulo the paper's p^2 moduli (Section 6.2.2) and an odd composite square:
+    Python big integers on random operands, and the (q-1)^2 K closed form with K across the
+    oracle's 64-term reduction."""
+    rng = np.random.default_rng(16)
+    q = [127 ** 2, 251 ** 2, 9 ** 2]
+    L, M, N, K = 3, 6, 4, 131
+    A = np.stack([rng.integers(0, ql, (M, K)).astype(np.uint64) for ql in q])
+    B = np.stack([rng.integers(0, ql, (N, K)).astype(np.uint64) for ql in q])
+    C = O.ppmm(q, A, B)
+    for l in range(L):
+        for j in range(N):
+            for i in range(M):
+                assert int(C[l, j, i]) == sum(int(A[l, i, k]) * int(B[l, j, k]) for k in range(K)) % q[l]
+    K = 70_000
+    for ql in q:
+        C = O.ppmm([ql], np.full((1, 2, K), ql - 1, np.uint64), np.full((1, 2, K), ql - 1, np.uint64))
+        assert np.all(C == K % ql)
+
+
 def test_crt_decode_closed_form():
     P = SMALL2
     scale = P.Qp * (1 << P.log2_delta)
