@@ -252,7 +252,7 @@ extern "C" icm_status icm_fold_mc(const icm_fold_mc_args *p, uint64_t *dev_count
         if (e == cudaSuccess && a.hist) e = cudaMemsetAsync(dev_hist, 0, 2 * (p->n_bins + 2) * sizeof(uint64_t), st);
     }
     if (e != cudaSuccess) { icm::set_error(cudaGetErrorString(e)); return ICM_ECUDA; }
-    for (uint64_t done = 0; done < p->n_trials; done += FMC_TRIALS_PER_LAUNCH) {
+    for (uint64_t done = 0; done < p->n_trials; done += a.n) {           // a.n >= 1: no wrap-around
         a.t0 = p->trial0 + done;
         a.n = std::min<uint64_t>(FMC_TRIALS_PER_LAUNCH, p->n_trials - done);
         a.sums = dev_sums ? (float2 *)dev_sums + done : nullptr;
