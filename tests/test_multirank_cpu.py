@@ -127,3 +127,14 @@ def test_two_ranks_shard_the_folding_trials():
     assert np.array_equal(np.concatenate([s[2] for s in sums]), one["sk"])
     assert np.array_equal(np.concatenate([s[3] for s in sums]), one["sk1"])
     assert shard.trial_range(3, 4, 10) == (8, 2) and shard.trial_range(0, 4, 10) == (0, 3)
+
+
+def test_trial_ranges_tile_the_run():
+    """For every world size (also more ranks than trials) the ranks' ranges are consecutive, cover
+    [0, n) exactly and differ in length by at most one."""
+    for n in (0, 1, 7, 6001, 2**33 + 5):
+        for world in (1, 2, 3, 8, 13):
+            rs = [shard.trial_range(r, world, n) for r in range(world)]
+            assert rs[0][0] == 0 and sum(c for _, c in rs) == n
+            assert all(rs[i][0] + rs[i][1] == rs[i + 1][0] for i in range(world - 1))
+            assert max(c for _, c in rs) - min(c for _, c in rs) <= 1
