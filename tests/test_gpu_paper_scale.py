@@ -6,7 +6,9 @@ warps), with the database resident (206 GB).
 * CCMM residues on sampled rows (a-part rows and b-rows spread over all eight database blocks, in
   every column and limb) equal the oracle's product of the same rows.
 * Decrypted numerators of all 113,770,496 (eye, rotation, code) pairs equal the cleartext inner
-  products <c'_db, c'_q> (Section 2.1.3), so decoded distances and match bits are exact."""
+  products <c'_db, c'_q> (Section 2.1.3), so decoded distances and match bits are exact.
+* Rescaled by Q' (the benchmark's rescaling leg): the sampled rows equal the oracle's rescaling of
+  the oracle's product, and all pairs decrypt exactly at the query modulus."""
 import gc
 
 import numpy as np
@@ -64,6 +66,16 @@ def _check_paper_shape():
         assert np.array_equal(O.match_bits(dec_num, den), O.match_bits(num, den))
         mb = O.match_bits(num, den)
         assert all(mb[eye, row] for row, (eye, _) in W.planted.items())
+
+        # rescaled by Q': sampled residues against the oracle, every pair decrypted at modulus Q
+        r = eng.rescale(s)
+        rdec = eng.decrypt(r)
+        torch.cuda.synchronize()
+        Lq = P.n_limbs_q
+        rres = r.buf[: Lq * ncol * M * 8].view(torch.int64).view(Lq, ncol, M)
+        rgot = rres.index_select(2, torch.from_numpy(sel).to(rres.device)).cpu().numpy().view(np.uint64)
+        assert np.array_equal(rgot, O.rescale(P, want))
+        assert np.array_equal(rdec.cpu().numpy(), inner)
     finally:
         C.icm_ctx_set_variant(eng.ctx, 0)
 

@@ -283,9 +283,9 @@ def test_ccmm_tcgen05_odd_modulus_count():
 # ----------------------------------------------------------------------------- rescaling by Q'
 
 def test_rescale_bit_exact(tiny, gpu_run):
-    """Rescaling by Q' on the GPU gives the oracle's residues at modulus Q (the correction v is
-    decided in IEEE double on both sides), for the CCMM result and for the folded scores, and the
-    fold of rescaled scores equals the oracle's fold at the rescaled level."""
+    """Rescaling by Q' on the GPU gives the oracle's residues at modulus Q (the correction v comes
+    from the same 64.64-bit fixed-point sum on both sides), for the CCMM result and for the folded
+    scores, and the fold of rescaled scores equals the oracle's fold at the rescaled level."""
     P, eng = tiny["P"], gpu_run["eng"]
     r = eng.rescale(gpu_run["s"])
     rf = eng.rescale(gpu_run["f"])
