@@ -76,8 +76,6 @@ def lib():
         _lib.orc_hd_counts.argtypes = [i32, i32, i32, vp, vp, vp, vp, vp, vp]
         _lib.orc_negacyclic_mul.restype = None
         _lib.orc_negacyclic_mul.argtypes = [vp, vp, i32, u64, vp]
-        _lib.orc_rescale.restype = None
-        _lib.orc_rescale.argtypes = [i32, i32, vp, ctypes.c_size_t, vp, vp]
         _lib.orc_omp_threads.restype = i32
         _lib.orc_omp_threads.argtypes = []
     return _lib
@@ -454,15 +452,46 @@ def crt_decode(P: Params, D: np.ndarray) -> np.ndarray:
     return nums.reshape(D.shape[1:]), worst
 
 
-def rescale(P: Params, C: np.ndarray) -> np.ndarray:
-    """Rescaling by Q' (orc_rescale): residues C [L][...] modulo Q_db = Q Q' -> [L_q][...] modulo
-    Q, x' = round(x / Q') with the base-conversion correction from a 64-bit fixed-point sum."""
-    L, Lq = P.n_limbs, P.n_limbs_q
+def crt_value(P: Params, C: np.ndarray) -> np.ndarray:
+    """The integers x in [0, Q_db) whose residues modulo q_0 .. q_{L-1} are C [L][...] (Chinese
+    remainder theorem, x = sum_l C_l (Q_db / q_l) ((Q_db / q_l)^-1 mod q_l) mod Q_db), as an object
+    array of Python integers shaped like C[0]."""
+    q = [int(v) for v in P.q]
+    Qdb = P.Qdb
+    L = C.shape[0]
     flat = np.ascontiguousarray(C.reshape(L, -1), np.uint64)
-    out = np.zeros((Lq, flat.shape[1]), np.uint64)
-    q = np.array(P.q, np.uint64)
-    lib().orc_rescale(L, Lq, _p(q), flat.shape[1], _p(flat), _p(out))
+    x = np.zeros(flat.shape[1], dtype=object)
+    for l in range(L):
+        hat = Qdb // q[l]
+        x = x + flat[l].astype(object) * (hat * pow(hat, -1, q[l]))
+    return (x % Qdb).reshape(C.shape[1:])
+
+
+def rescale(P: Params, C: np.ndarray) -> np.ndarray:
+    """Rescaling by Q' (Section 2.2.2, Maintenance: RS divides by a factor of the modulus and
+    rounds to the nearest integer).  The dropped factor is Q' = q_{L_q} ... q_{L-1}, so each
+    coefficient x of Z_{Q Q'} (residues C [L][...]) becomes x' = round(x / Q') mod Q, returned as
+    its residues [L_q][...] modulo q_0 .. q_{L_q - 1}.  Computed on the exact integers:
+    round(x / Q') = floor((2x + Q') / (2Q')); Q' is odd, so x / Q' is never a half-integer and the
+    rounding has no ties.  Any representative of x modulo Q Q' gives the same x' modulo Q."""
+    Lq = P.n_limbs_q
+    Qp, Q = P.Qp, P.Q
+    x = crt_value(P, C).reshape(-1)
+    xr = ((2 * x + Qp) // (2 * Qp)) % Q
+    out = np.zeros((Lq, x.shape[0]), np.uint64)
+    for j in range(Lq):
+        out[j] = (xr % int(P.q[j])).astype(np.uint64)
     return out.reshape((Lq,) + C.shape[1:])
+
+
+def rescale_half_distance(P: Params, C: np.ndarray) -> np.ndarray:
+    """For every coefficient x (residues C [L][...]): the exact distance of x / Q' from the
+    nearest half-integer, as the pair (|2 (x mod Q') - Q'|, 2 Q') of Python integers (distance =
+    first / second).  Test support: a fast rescaling that estimates the quotient in fixed point may
+    round either way only where this distance is below its stated error bound."""
+    Qp = P.Qp
+    y = crt_value(P, C) % Qp
+    return np.abs(2 * y - Qp), 2 * Qp
 
 
 def crt_decode_q(P: Params, D: np.ndarray) -> tuple:

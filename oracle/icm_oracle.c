@@ -331,56 +331,6 @@ void orc_decrypt_rows(int L, const uint64_t *q, int ndb, int h, uint64_t seed, c
     free(sdbs); free(sdb);
 }
 
-/* ---------------------------------------------------------------- rescaling ---- */
-
-static uint64_t mulm(uint64_t a, uint64_t b, uint64_t q) { return (uint64_t)(((u128)a * b) % q); }
-static uint64_t powm(uint64_t a, uint64_t e, uint64_t q) {
-    uint64_t r = 1 % q;
-    a %= q;
-    while (e) { if (e & 1) r = mulm(r, a, q); a = mulm(a, a, q); e >>= 1; }
-    return r;
-}
-
-/* Rescaling by Q' (Section 2.2.2, Maintenance: RS divides a ciphertext by a modulus factor and
- * rounds; here the dropped factor is Q' = q_Lq ... q_{L-1}, so the result lives modulo
- * Q = q_0 ... q_{Lq-1}).  For every coefficient x in Z_{Q Q'} given by its residues x_l:
- *   yh_i = x_i (Q'/q_i)^{-1} mod q_i                         for the limbs i of Q',
- *   F_i  = floor(yh_i floor(2^128 / q_i) / 2^64)             (yh_i / q_i in 64-bit fixed point),
- *   v    = floor((sum_i F_i + 2^63) / 2^64)                  (the nearest integer to sum yh_i / q_i),
- *   y    = sum_i yh_i (Q'/q_i) - v Q'                        (x = y mod Q', |y| <= Q'/2),
- *   x'_j = (x_j - y mod q_j) Q'^{-1} mod q_j                 for the limbs j of Q,
- * i.e. x' = (x - y) / Q' = round(x / Q') mod Q; each F_i is short of 2^64 yh_i / q_i by less than
- * one, so only where sum yh_i / q_i lies within (L - Lq) 2^-64 of a half-integer may v, and x',
- * differ by one from the exact rounding (within the rounding error of rescaling).
- * in: [L][n], out: [Lq][n]. */
-void orc_rescale(int L, int Lq, const uint64_t *q, size_t n, const uint64_t *in, uint64_t *out) {
-#pragma omp parallel for schedule(static)
-    for (size_t c = 0; c < n; ++c) {
-        uint64_t yh[64];
-        u128 S = 0;
-        for (int i = Lq; i < L; ++i) {
-            uint64_t qhat = 1;                            /* Q' / q_i mod q_i */
-            for (int k = Lq; k < L; ++k) if (k != i) qhat = mulm(qhat, q[k] % q[i], q[i]);
-            yh[i] = mulm(in[(size_t)i * n + c], powm(qhat, q[i] - 2, q[i]), q[i]);
-            const u128 C = (~(u128)0) / q[i];             /* floor(2^128 / q_i), q_i odd */
-            S += (u128)yh[i] * C >> 64;                   /* yh_i C < 2^128 since yh_i < q_i */
-        }
-        const uint64_t v = (uint64_t)((S + ((u128)1 << 63)) >> 64);
-        for (int j = 0; j < Lq; ++j) {
-            uint64_t y = 0, qp = 1;
-            for (int i = Lq; i < L; ++i) {
-                uint64_t qhat = 1;                        /* Q' / q_i mod q_j */
-                for (int k = Lq; k < L; ++k) if (k != i) qhat = mulm(qhat, q[k] % q[j], q[j]);
-                y = (uint64_t)(((u128)y + mulm(yh[i] % q[j], qhat, q[j])) % q[j]);
-                qp = mulm(qp, q[i] % q[j], q[j]);
-            }
-            y = (uint64_t)(((u128)y + q[j] - mulm(v % q[j], qp, q[j])) % q[j]);
-            const uint64_t d = (uint64_t)(((u128)in[(size_t)j * n + c] + q[j] - y) % q[j]);
-            out[(size_t)j * n + c] = mulm(d, powm(qp, q[j] - 2, q[j]), q[j]);
-        }
-    }
-}
-
 /* ---------------------------------------------------------------- cleartext ---- */
 
 /* Fractional Hamming distance ingredients (Section 2.1.1, Eq. (1)) on packed 64-bit words:

@@ -376,36 +376,56 @@ def test_ccmm_decrypts_to_cleartext_inner_products(P):
 
 # ----------------------------------------------------------------------------- rescaling
 
+def _from_residues(res, moduli):
+    """Test-side Chinese remaindering: the integer in [0, prod moduli) with the given residues,
+    found by Garner-style incremental lifting (a different route from the oracle's sum formula)."""
+    x, m = 0, 1
+    for r, qj in zip(res, moduli):
+        t = ((int(r) - x) * pow(m, -1, qj)) % qj
+        x, m = x + m * t, m * qj
+    return x
+
+
 @pytest.mark.parametrize("P", [SMALL, SMALL2])
 def test_rescale_is_rounded_division(P):
-    """Rescaling by Q' (Section 2.2.2, Maintenance) equals round(x / Q') mod Q computed with
-    Python integers, on random coefficients and on the closed-form cases k Q' + e (|e| < Q'/2,
-    which round to k) and the ends of [0, Q Q')."""
+    """Rescaling by Q' (Section 2.2.2, Maintenance: divide by the dropped modulus factor and
+    round).  Checked by what characterises the nearest integer, not by the oracle's formula:
+    (i) for random x, the result x' is the unique class modulo Q with |x - Q' x'| <= (Q' - 1) / 2
+    (centred modulo Q Q'); (ii) closed forms: k Q' + e rounds to k for every |e| <= (Q' - 1) / 2,
+    including both edges next to the (never reached) half-integer; (iii) the ends of [0, Q Q')."""
     rng = np.random.default_rng(3)
     Qdb, Qp, Q = P.Qdb, P.Qp, P.Q
+    Lq = P.n_limbs_q
     xs = [int.from_bytes(rng.bytes(64), "little") % Qdb for _ in range(400)]
     ks = [0, 1, 2, Q // 3, Q - 1]
-    es = [0, 1, -1, Qp // 2, -(Qp // 2), Qp // 3]
-    xs += [(k * Qp + e) % Qdb for k in ks for e in es] + [0, Qdb - 1, Qp // 2, Qp // 2 + 1]
-    C = np.array([[x % ql for x in xs] for ql in P.q], np.uint64)
+    h = (Qp - 1) // 2
+    es = [0, 1, -1, h, -h, h - 1, -(h - 1), Qp // 3]
+    closed = [(k, e) for k in ks for e in es]
+    xs_closed = [(k * Qp + e) % Qdb for k, e in closed]
+    xs_all = xs + xs_closed + [0, Qdb - 1]
+    C = np.array([[x % ql for x in xs_all] for ql in P.q], np.uint64)
     got = O.rescale(P, C)
-    # exact nearest integer; within (L - L_q) 2^-64 of a half-integer the fixed-point correction
-    # may take either neighbour (x = floor(Q'/2) is such a case: x / Q' = 1/2 - 1/(2 Q'))
-    for idx, x in enumerate(xs):
-        want = (2 * x + Qp) // (2 * Qp)
-        near_tie = abs(2 * (x % Qp) - Qp) < (Qp >> 60)
-        cands = [want, want - 1, want + 1] if near_tie else [want]
-        res = [int(got[j, idx]) for j in range(P.n_limbs_q)]
-        assert any(res == [(c % Q) % qj for qj in P.q[: P.n_limbs_q]] for c in cands), (idx, x)
-        if not near_tie:
-            assert res == [(want % Q) % qj for qj in P.q[: P.n_limbs_q]]
-    assert any(abs(2 * (x % Qp) - Qp) < (Qp >> 60) for x in xs)        # the tie window is exercised
-    # the closed-form cases directly: k Q' + e rounds to k (|e| <= Q'/3, away from the ties)
-    for k in ks:
-        for e in es:
-            if abs(e) <= Qp // 3 and (k * Qp + e) % Qdb == k * Qp + e:
-                idx = xs.index((k * Qp + e) % Qdb)
-                assert [int(got[j, idx]) for j in range(P.n_limbs_q)] == [k % qj for qj in P.q[: P.n_limbs_q]]
+    assert got.shape == (Lq, len(xs_all))
+    moduli = [int(v) for v in P.q[:Lq]]
+    xp = [_from_residues(got[:, i], moduli) for i in range(len(xs_all))]
+    # (i) nearest-integer property for every input
+    for x, y in zip(xs_all, xp):
+        d = (x - Qp * y) % Qdb
+        if d > Qdb // 2:
+            d -= Qdb
+        assert abs(d) <= h, (x, y)
+    # (ii) closed forms
+    for (k, e), y in zip(closed, xp[len(xs):len(xs) + len(closed)]):
+        assert y == k % Q, (k, e)
+    # (iii) the ends: 0 -> 0 and Q Q' - 1 (just below Q x Q') -> Q = 0 mod Q
+    assert xp[-2] == 0 and xp[-1] == 0
+    # the exact half-distance that the GPU parity tests use: zero never occurs (Q' odd), and the
+    # edges e = +-(Q' - 1)/2 sit at the smallest possible distance 1 / (2 Q')
+    num, den = O.rescale_half_distance(P, C)
+    assert den == 2 * Qp and min(num) >= 1
+    for (k, e), n in zip(closed, num[len(xs):len(xs) + len(closed)]):
+        if abs(e) == h and (k * Qp + e) % Qdb == k * Qp + e:
+            assert n == 1
 
 
 @pytest.mark.parametrize("P", [SMALL, SMALL2])
