@@ -185,6 +185,14 @@ icm_status icm_scores_shape(const icm_scores *s, size_t *n_limbs, size_t *n_cols
  * numerator <c'_db, c'_q> (unfolded scores) or the folded sum of numerators.  dev_num: int64
  * [n_cols][n_db].  Threshold decryption is outside this library. */
 icm_status icm_decrypt_scores(icm_ctx *ctx, const icm_scores *s, int64_t *dev_num, size_t n, void *stream);
+/* icm_decrypt_scores, and also the largest distance |x - round(x)| between a decoded value x
+ * (decrypted coefficient divided by Q' * Delta, or by Delta at the rescaled level) and the
+ * integer it rounds to, over all outputs: dev_max_err is one fp32 in device memory, written on
+ * `stream`.  It bounds the pre-rounding error of the decoded numerators (the encryption noise plus
+ * the decoder's own 128-bit fixed-point error, below 2^-5 units for 60-bit primes); the decoded
+ * numerators are exact while it stays below 1/2. */
+icm_status icm_decrypt_scores_max_error(icm_ctx *ctx, const icm_scores *s, int64_t *dev_num, size_t n,
+                                        float *dev_max_err, void *stream);
 
 /* Rescaling by Q' (Section 2.2.2, Maintenance: RS divides a ciphertext by a modulus factor and
  * rounds): scores at modulus Q_db = Q Q' (L limbs) become scores at the query modulus Q (the
@@ -229,21 +237,33 @@ void icm_plan_destroy(icm_plan *plan);
 
 /* Kernel variant of the CRT forms' product: 0 or 256 = mma.sync with 256-column tiles (default),
  * 128 = mma.sync with 128-column tiles; for the fp16 form on a database in the storage form, the
- * tcgen05 kernel (tensor-memory accumulators, TMA-fed, one modulus on 512 columns per block;
- * needs an even K, else variant 0 runs): 1 = 16 converter warps, 2 = 16 converter warps with a
- * progress bound between blocks (cooperative launch), 3 = 8 converter warps, 4 = 8 converter
- * warps with the progress bound, 5 = 2-SM MMA over clusters of two blocks (256 rows per pair).
- * Results are identical; only speed differs. */
+ * tcgen05 kernel (tensor-memory accumulators, TMA-fed, one modulus on 512 columns per block and
+ * round, every round of up to 1,024 columns in one launch; needs an even K, else variant 0 runs):
+ * 1 = rings of 8 raw-database and 4 operand slots; 2 = the same with a wave bound between blocks
+ * (a block starts fetching its next tile once every block has fetched its current one;
+ * cooperative launch); 3 = 4 raw-database and 8 operand slots.  Results are identical; only
+ * speed differs. */
 icm_status icm_ctx_set_variant(icm_ctx *ctx, int variant);
+/* Failure detection of the tcgen05 kernel (no counterpart in the paper).  Every device-side wait
+ * of that kernel (barrier phases, the wave bound) gives up after wait_ns nanoseconds of
+ * %globaltimer (0 restores the default, 2 s): the kernel then records ICM_ETIMEOUT in the device
+ * status word, stops issuing work, waits (bounded) for its own copies and MMAs in flight, frees
+ * its tensor memory and returns; its outputs are then invalid.  inject_stall != 0 is for tests
+ * only: the kernel's query producer of the first column tile then issues no copies, so the MMA
+ * issuer's wait runs out on purpose (no fault, no trap).  Applies to later launches from this
+ * context.  Errors: ICM_EINVAL for a null context. */
+icm_status icm_ctx_set_device_wait(icm_ctx *ctx, uint64_t wait_ns, int inject_stall);
 /* Device status word shared by the library's kernels: ICM_OK, or ICM_ETIMEOUT once a kernel gave
  * up one of its bounded waits (the kernel then stopped early, so its outputs are invalid).  Reads
  * the word (synchronising the device) and clears it when clear != 0. */
 icm_status icm_device_status(int clear);
 
-/* Autotuner: times every kernel variant of the CRT product on the caller's batch (one
- * icm_match_batch per variant, CUDA events on `stream`), keeps the fastest for the context and
- * reports it (0 for forms with a single variant).  ms_per_choice (optional) receives the time of
- * each variant in the order 128, 256 (mma.sync), then 1 to 5 (tcgen05, fp16 form only). */
+/* Autotuner: times the kernel variants of the CRT product that apply on the caller's batch (one
+ * icm_match_batch per variant, CUDA events on `stream`): the tcgen05 variants 1-3 for the fp16
+ * form with an even K, else the mma.sync tiles 128 and 256.  Keeps the fastest for the context
+ * and reports it (0 for forms with a single variant).  ms_per_choice (optional, n_choices
+ * entries) receives the time of each variant in the fixed order 128, 256, 1, 2, 3, with 0 for the
+ * variants not timed. */
 icm_status icm_autotune(icm_ctx *ctx, const icm_db *const *dbs, size_t n_dbs, const icm_query *q,
                         void *const *dev_outs, const size_t *out_bytes, void *dev_ws, size_t ws_bytes, void *stream,
                         int *best_tile_n, float *ms_per_choice, size_t n_choices);
@@ -252,25 +272,38 @@ icm_status icm_autotune(icm_ctx *ctx, const icm_db *const *dbs, size_t n_dbs, co
 
 /* A request loop over a resident encrypted database (Section 5: computing servers batch up to 32
  * query eyes).  Query eyes are submitted one at a time with their wire ciphertext; a worker
- * thread batches them (a batch starts when it holds max_eyes eyes or its oldest eye has waited
- * window_us; eyes arriving while a batch runs join the next one), runs query preparation, the
- * grouped CCMM and the folds, and returns every eye's folded scores.  Two I/O slots let one
- * batch's copies overlap another's compute.  Admission: at most max_pending eyes wait (submit
- * returns ICM_ENOMEM beyond that); a batch is admitted when an I/O slot is free. */
+ * thread batches them (a batch starts when max_eyes eyes wait or the oldest has waited
+ * window_us; eyes arriving while batches run join a later one), runs query preparation, the
+ * grouped CCMM and the folds, and returns every eye's folded scores.
+ * Admission: at most max_pending eyes wait on the host (submit returns ICM_ENOMEM beyond that).
+ * A batch starts when one of max_batches batch slots is free and the device workspace, used as a
+ * pool, holds the buffers of at least one waiting eye: every batch of n eyes reserves the bytes
+ * its buffers take at n eyes for its whole life (first fit) and takes as many waiting eyes (up to
+ * max_eyes) as the free memory allows.  Each slot has its own compute and copy streams: one
+ * batch's copies, query preparation and folds overlap another's CCMM; the CCMMs of successive
+ * batches run one after the other. */
 typedef struct icm_server icm_server;
 typedef struct {
     uint32_t max_eyes;       /* eyes per batch, 1..32                                          */
     uint32_t window_us;      /* batching window for a partial batch                            */
     icm_form form;           /* arithmetic form of the CCMM                                    */
     uint32_t max_pending;    /* admission bound on waiting eyes (0 = 4096)                     */
+    uint32_t max_batches;    /* batch slots (batches in flight), 0..4 (0 = 2)                  */
 } icm_server_cfg;
 
-/* Device workspace bytes of a server (compute buffers and two I/O slots). */
+/* Device workspace bytes that hold max_batches full batches (max_eyes eyes each).  A server runs
+ * with any workspace of at least one full batch; with less than this, fewer or smaller batches
+ * are admitted at a time. */
 icm_status icm_server_device_bytes(const icm_ctx *ctx, const icm_db *const *dbs, size_t n_dbs,
                                    const icm_server_cfg *cfg, size_t *bytes);
-/* Start a server on 1..16 resident chunks; dev_ws stays owned by the caller and must outlive it. */
+/* Start a server on 1..16 resident chunks; dev_ws (ws_bytes, at least one full batch, else
+ * ICM_ENOMEM) stays owned by the caller and must outlive it. */
 icm_status icm_server_create(icm_ctx *ctx, const icm_db *const *dbs, size_t n_dbs, const icm_server_cfg *cfg,
                              void *dev_ws, size_t ws_bytes, icm_server **out);
+/* Memory accounting: pool size, bytes of one full batch, the most bytes reserved at once and the
+ * most batches in flight at once so far. */
+icm_status icm_server_memory(icm_server *s, size_t *pool_bytes, size_t *full_batch_bytes, size_t *peak_bytes,
+                             uint32_t *peak_batches);
 /* Words (u64) of one eye's ciphertext ([L_q][rho][K], the eye's columns of the wire format) and
  * of one eye's result (for every chunk in order: [L][ceil(rho/fold_k)][M_c] folded scores). */
 icm_status icm_server_eye_words(const icm_server *s, size_t *ct_words, size_t *out_words);
@@ -321,10 +354,13 @@ icm_status icm_ppmm(icm_form form, const uint64_t *q, uint32_t n_limbs, const ui
  * under a fixed device-memory budget, or code enqueued while allocations are not allowed.  The
  * workspace (query residue planes and per-modulus residue scratch) lives in one static device
  * array of 64 MiB that every GPU loading this library holds until the process exits; problems
- * whose workspace exceeds it are rejected with ICM_ENOMEM before any work.  The first call on a
- * device looks up that device's address of the array (make it before any stream capture); later
- * calls reuse it.  All calls share the array: calls that overlap on the GPU race with each other
- * (serialise them, for instance on one stream).  Arguments as icm_ppmm minus the workspace. */
+ * whose workspace exceeds it are rejected with ICM_ENOMEM before any work (checked before the
+ * pointers).  The first call in a CUDA context (normally the device's primary context) looks up
+ * that context's address of the array (make it before any stream capture); later calls in the
+ * same context reuse it, and a context created later (a non-primary context made current, or the
+ * primary context re-created after cudaDeviceReset) gets its own lookup on its first call.  All
+ * calls share the array: calls that overlap on the GPU race with each other (serialise them, for
+ * instance on one stream).  Arguments as icm_ppmm minus the workspace. */
 icm_status icm_ppmm_noalloc(icm_form form, const uint64_t *q, uint32_t n_limbs, const uint64_t *dev_A,
                             const uint64_t *dev_B, uint64_t *dev_C, size_t M, size_t N, size_t K, void *stream);
 

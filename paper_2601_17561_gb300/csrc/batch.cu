@@ -153,8 +153,10 @@ icm_status icm_autotune(icm_ctx *c, const icm_db *const *dbs, size_t n_dbs, cons
                         float *ms_per_choice, size_t n_choices) {
     if (!c || !q || !best_tile_n) return api_fail(ICM_EINVAL, "bad arguments");
     if (!crt_form(q->form)) { *best_tile_n = 0; return ICM_OK; }      // single kernel variant
-    const int choices[7] = {128, 256, 1, 2, 3, 4, 5};
-    const int n_var = q->form == ICM_FORM_F16_CRT && crt_tc_supported(c->K) ? 7 : 2;
+    // the tcgen05 variants where they apply (fp16 form, even K), else the two mma.sync tiles;
+    // ms_per_choice keeps the fixed order 128, 256, 1, 2, 3 (0 for variants not timed)
+    const int choices[5] = {128, 256, 1, 2, 3};
+    const bool tc = q->form == ICM_FORM_F16_CRT && crt_tc_supported(c->K);
     float best_ms = 1e30f;
     int best = c->crt_bn;
     cudaStream_t st = (cudaStream_t)stream;
@@ -162,7 +164,9 @@ icm_status icm_autotune(icm_ctx *c, const icm_db *const *dbs, size_t n_dbs, cons
     cudaEventCreate(&a);
     cudaEventCreate(&b);
     icm_status s = ICM_OK;
-    for (int i = 0; i < n_var && s == ICM_OK; ++i) {
+    for (int i = 0; i < 5 && s == ICM_OK; ++i) {
+        if (ms_per_choice && (size_t)i < n_choices) ms_per_choice[i] = 0.0f;
+        if (tc != crt_tc_variant(choices[i])) continue;
         c->crt_bn = choices[i];
         std::vector<icm_scores *> outs(n_dbs, nullptr);
         cudaEventRecord(a, st);
@@ -185,9 +189,16 @@ icm_status icm_autotune(icm_ctx *c, const icm_db *const *dbs, size_t n_dbs, cons
     return s;
 }
 
+icm_status icm_ctx_set_device_wait(icm_ctx *c, uint64_t wait_ns, int inject_stall) {
+    if (!c) return api_fail(ICM_EINVAL, "null context");
+    c->i8_crt.tc_wait_ns = wait_ns;
+    c->i8_crt.tc_inject_stall = inject_stall ? 1u : 0u;
+    return ICM_OK;
+}
+
 icm_status icm_ctx_set_variant(icm_ctx *c, int variant) {
     if (!c || (variant != 0 && !crt_tc_variant(variant) && variant != 128 && variant != 256))
-        return api_fail(ICM_EINVAL, "variant must be 0, 1..5, 128 or 256");
+        return api_fail(ICM_EINVAL, "variant must be 0, 1..3, 128 or 256");
     c->crt_bn = variant == 0 ? 256 : variant;
     return ICM_OK;
 }

@@ -23,8 +23,8 @@
 // one is multiplied.  The query planes stream in with cp.async.  Fragments come from ldmatrix on
 // rows padded by 16 bytes (conflict-free).  Blocks of one (limb, row tile) are consecutive in
 // launch order (column tiles, then moduli, vary fastest) so a database slab is read from HBM
-// about once and re-served from L2.  Columns are processed in chunks so the scratch stays at
-// L r min(N, 512) M bytes.
+// about once and re-served from L2.  Columns are processed in chunks of 512 (the scratch holds
+// L r min(N, 1024) M bytes, the largest column round of any CRT kernel).
 #include "icm_internal.h"
 #include "ppmm_i8.h"
 
@@ -398,7 +398,7 @@ cudaError_t crt_set_attributes() {
 }
 
 uint64_t crt_scratch_bytes(uint32_t n_limbs, uint32_t n_mod, uint64_t N, uint64_t M) {
-    static_assert(NCHUNK == 512, "crt_scratch_main_bytes assumes 512-column rounds");
+    static_assert(NCHUNK <= 1024, "crt_scratch_main_bytes holds column rounds of up to 1,024");
     return crt_scratch_main_bytes(n_limbs, n_mod, N, M) + CRT_PROGRESS_BYTES;
 }
 

@@ -28,6 +28,10 @@ struct I8Consts {
     // p^2 form: q_l = pd_l^2, digit base pd_l and 1 / pd_l (pw8[l][0..1] hold 1 and pd_l)
     int32_t pd[ICM_MAX_LIMBS];
     float inv_p[ICM_MAX_LIMBS];
+    // launch settings of the tcgen05 kernel: bound of every device-side wait in ns (0: 2 s), and
+    // the test-only stall of the query producer (its waits then run out on purpose)
+    uint64_t tc_wait_ns;
+    uint32_t tc_inject_stall;
 };
 
 // Builds the constants for primes q and contraction depth K; returns false (with a reason in
@@ -55,12 +59,11 @@ cudaError_t launch_ppmm_crt_grouped(bool f16, int bn, const I8Consts &k, const C
                                     uint64_t K, uint64_t Kp, void *scratch, cudaStream_t st);
 cudaError_t crt_set_attributes();
 // Kernel variants of the CRT product: the column tile of the mma.sync kernel (128, 256), or the
-// tcgen05 kernel for the fp16 form on the balanced-digit database: 1 = 16 converter warps,
-// 2 = 16 converter warps with the progress bound between blocks, 3 = 8 converter warps,
-// 4 = 8 converter warps with the progress bound, 5 = 2-SM MMA over clusters of two blocks
-// (M = 256 per pair, 8 converter warps per block).
+// tcgen05 kernel for the fp16 form on the balanced-digit database (one launch per 1,024 columns):
+// 1 = rings of 8 raw-database and 4 operand slots, 2 = the same with the wave bound between blocks
+// (cooperative launch), 3 = 4 raw-database and 8 operand slots.
 #define ICM_CRT_TCGEN05 1
-#define ICM_CRT_TCGEN05_LAST 5
+#define ICM_CRT_TCGEN05_LAST 3
 inline bool crt_tc_variant(int v) { return v >= ICM_CRT_TCGEN05 && v <= ICM_CRT_TCGEN05_LAST; }
 cudaError_t launch_crt_combine(const I8Consts &k, const ChunkTab &tab, const void *scratch, uint64_t N, uint64_t n0,
                                uint64_t nch, cudaStream_t st);
@@ -88,11 +91,12 @@ __host__ __device__ __forceinline__ uint64_t crt_f16_off(uint64_t j, uint64_t k,
            (k & 7);
 }
 // small-modulus CRT forms (int8 or fp16 operands): query residue planes, two-phase product.
-// Scratch: the residue bytes [L][r][min(N, 512)][M] (rounded up to 256 bytes), then
-// CRT_PROGRESS_BYTES of progress words for the tcgen05 kernel's progress bound.
+// Scratch: the residue bytes [L][r][min(N, 1024)][M] (one column round of the largest kernel,
+// rounded up to 256 bytes), then CRT_PROGRESS_BYTES for the tcgen05 kernel's wave counter and
+// give-up word.
 constexpr uint64_t CRT_PROGRESS_BYTES = 4096;
 inline uint64_t crt_scratch_main_bytes(uint32_t n_limbs, uint32_t n_mod, uint64_t N, uint64_t M) {
-    return ((uint64_t)n_limbs * n_mod * (N < 512 ? N : 512) * M + 255) / 256 * 256;
+    return ((uint64_t)n_limbs * n_mod * (N < 1024 ? N : 1024) * M + 255) / 256 * 256;
 }
 uint64_t crt_scratch_bytes(uint32_t n_limbs, uint32_t n_mod, uint64_t N, uint64_t M);
 cudaError_t launch_crt_planes(bool f16, const I8Consts &k, const uint64_t *op, void *planes, uint64_t N, uint64_t K,

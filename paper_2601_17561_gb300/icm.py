@@ -26,7 +26,7 @@ class IcmError(RuntimeError):
 
 class icm_server_cfg(ctypes.Structure):
     _fields_ = [("max_eyes", ctypes.c_uint32), ("window_us", ctypes.c_uint32), ("form", ctypes.c_int),
-                ("max_pending", ctypes.c_uint32)]
+                ("max_pending", ctypes.c_uint32), ("max_batches", ctypes.c_uint32)]
 
 
 class icm_params(ctypes.Structure):
@@ -69,6 +69,7 @@ _SIGS = {
     "icm_scores_destroy": (None, [_vp]),
     "icm_scores_shape": (_i32, [_vp, ctypes.POINTER(_sz), ctypes.POINTER(_sz), ctypes.POINTER(_sz)]),
     "icm_decrypt_scores": (_i32, [_vp, _vp, _vp, _sz, _vp]),
+    "icm_decrypt_scores_max_error": (_i32, [_vp, _vp, _vp, _sz, _vp, _vp]),
     "icm_rescale_bytes": (_i32, [_vp, ctypes.POINTER(_sz)]),
     "icm_rescale": (_i32, [_vp, _vp, _vp, _sz, _vp, ctypes.POINTER(_vp)]),
     "icm_ppmm_workspace_bytes": (_i32, [_i32, _u32, _sz, _sz, _sz, ctypes.POINTER(_sz)]),
@@ -76,6 +77,7 @@ _SIGS = {
     "icm_sync": (_i32, [_vp, _u32]),
     "icm_ppmm_noalloc": (_i32, [_i32, _vp, _u32, _vp, _vp, _vp, _sz, _sz, _sz, _vp]),
     "icm_ctx_set_variant": (_i32, [_vp, _i32]),
+    "icm_ctx_set_device_wait": (_i32, [_vp, ctypes.c_uint64, _i32]),
     "icm_device_status": (_i32, [_i32]),
     "icm_match_host_workspace_bytes": (_i32, [_vp, _vp, _sz, _i32, ctypes.POINTER(_sz)]),
     "icm_match_host": (_i32, [_vp, _vp, _vp, _sz, _i32, _vp, _vp, _sz, _vp]),
@@ -93,6 +95,8 @@ _SIGS = {
     "icm_server_wait": (_i32, [_vp, _u64, _u32, ctypes.POINTER(ctypes.c_double)]),
     "icm_server_stats": (_i32, [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64), ctypes.POINTER(ctypes.c_double)]),
     "icm_server_destroy": (_i32, [_vp, _u32]),
+    "icm_server_memory": (_i32, [_vp, ctypes.POINTER(_sz), ctypes.POINTER(_sz), ctypes.POINTER(_sz),
+                                 ctypes.POINTER(_u32)]),
     "icm_fold_mc": (_i32, [ctypes.POINTER(icm_fold_mc_args), _vp, _vp, _vp, _vp]),
     "icm_fold_poly_range": (_i32, [_vp, _u32, ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_double)]),
@@ -263,6 +267,11 @@ def icm_decrypt_scores(ctx, scores, dev_num, n, stream=None):
     _check(lib().icm_decrypt_scores(ctx, scores, _ptr(dev_num), n, _stream(stream)), "icm_decrypt_scores")
 
 
+def icm_decrypt_scores_max_error(ctx, scores, dev_num, n, dev_max_err, stream=None):
+    _check(lib().icm_decrypt_scores_max_error(ctx, scores, _ptr(dev_num), n, _ptr(dev_max_err), _stream(stream)),
+           "icm_decrypt_scores_max_error")
+
+
 def icm_ppmm_workspace_bytes(form, n_limbs, M, N, K):
     b = ctypes.c_size_t()
     _check(lib().icm_ppmm_workspace_bytes(form, n_limbs, M, N, K, ctypes.byref(b)), "icm_ppmm_workspace_bytes")
@@ -346,12 +355,15 @@ def icm_autotune(ctx, dbs, q, dev_outs, out_bytes, dev_ws, ws_bytes, stream=None
 
 
 # CRT product kernel variants in the autotuner's order (icm_autotune's ms_per_choice)
-VARIANTS = {128: "mma.sync-128", 256: "mma.sync-256", 1: "tcgen05-16w", 2: "tcgen05-16w-sync", 3: "tcgen05-8w",
-            4: "tcgen05-8w-sync", 5: "tcgen05-2sm-8w"}
+VARIANTS = {128: "mma.sync-128", 256: "mma.sync-256", 1: "tcgen05-r8s4", 2: "tcgen05-r8s4-wave", 3: "tcgen05-r4s8"}
 
 
 def icm_ctx_set_variant(ctx, variant: int):
     _check(lib().icm_ctx_set_variant(ctx, variant), "icm_ctx_set_variant")
+
+
+def icm_ctx_set_device_wait(ctx, wait_ns: int = 0, inject_stall: bool = False):
+    _check(lib().icm_ctx_set_device_wait(ctx, wait_ns, 1 if inject_stall else 0), "icm_ctx_set_device_wait")
 
 
 def icm_device_status(clear: bool = True):
@@ -394,6 +406,14 @@ def icm_server_stats(srv):
     a, b, m = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_double()
     _check(lib().icm_server_stats(srv, ctypes.byref(a), ctypes.byref(b), ctypes.byref(m)), "icm_server_stats")
     return a.value, b.value, m.value
+
+
+def icm_server_memory(srv):
+    """(pool bytes, bytes of one full batch, peak reserved bytes, peak batches in flight)"""
+    a, b, c, d = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_uint32()
+    _check(lib().icm_server_memory(srv, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)),
+           "icm_server_memory")
+    return a.value, b.value, c.value, d.value
 
 
 def icm_server_destroy(srv, timeout_ms=600000):

@@ -72,7 +72,9 @@ def test_autotune_keeps_results(setup):
     eng, dbs = setup["eng"], setup["dbs"]
     q = eng.prepare(setup["ct"], 3, "f16_crt")
     best, ms = eng.autotune(dbs, q)
-    assert best in (128, 256, 1, 2, 3, 4, 5) and all(m > 0 for m in ms)
+    # the fp16 form with an even K times the tcgen05 variants 1-3 (slots 2-4 of the fixed order
+    # 128, 256, 1, 2, 3) and not the mma.sync tiles
+    assert best in (1, 2, 3) and all(m > 0 for m in ms[2:5]) and ms[0] == 0 and ms[1] == 0
     outs = eng.match_batch(dbs, q)
     torch.cuda.synchronize()
     for s, ref in zip(outs, setup["ref"]):
@@ -92,7 +94,7 @@ def test_small_batches(setup, n_eyes):
         assert np.array_equal(s.residues(), ref[:, : n_eyes * 31, :])
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 def test_grouped_tcgen05_variant(setup, variant):
     """tcgen05 variants over uneven chunks (ragged row tiles, partial column tile)."""
     from paper_2601_17561_gb300 import icm as C
@@ -109,11 +111,11 @@ def test_grouped_tcgen05_variant(setup, variant):
         C.icm_ctx_set_variant(eng.ctx, 0)
 
 
-@pytest.mark.parametrize("variant", [2, 4, 5])
-def test_graph_replay_progress_bound_variant(setup, variant):
-    """The tcgen05 variants with the progress bound (cooperative launch, progress words reset by a
-    memset node) and the 2-SM variant (cluster launch) captured in the plan's CUDA graph: two
-    replays give the oracle's folded scores."""
+@pytest.mark.parametrize("variant", [1, 2, 3])
+def test_graph_replay_tcgen05_variant(setup, variant):
+    """The tcgen05 variants captured in the plan's CUDA graph (the wave variants as cooperative
+    launches with their counter reset by a memset node): two replays give the oracle's folded
+    scores."""
     from paper_2601_17561_gb300 import icm as C
     eng, dbs = setup["eng"], setup["dbs"]
     C.icm_ctx_set_variant(eng.ctx, variant)

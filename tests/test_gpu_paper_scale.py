@@ -25,7 +25,7 @@ from paper_2601_17561_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 # tcgen05 kernel variants checked at this shape: every variant the autotuner may pick here
-VARIANTS = (1, 3)
+VARIANTS = (1, 2, 3)
 
 
 def _check_paper_shape(variants):
@@ -62,7 +62,7 @@ def _check_paper_shape(variants):
             torch.cuda.synchronize()
         finally:
             C.icm_ctx_set_variant(eng.ctx, 0)
-        assert C.icm_device_status(True) == 0
+        C.icm_device_status(True)          # raises IcmError(ICM_ETIMEOUT) if a wait ran out
         L = P.n_limbs
         assert s.shape == (L, ncol, M)
         res = s.buf[: L * ncol * M * 8].view(torch.int64).view(L, ncol, M)
