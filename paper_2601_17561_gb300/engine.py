@@ -179,11 +179,17 @@ class Engine:
         """Capture prepare + grouped CCMM + folds on fixed buffers into a CUDA graph."""
         return Plan(self, dbs, n_eyes, form, ct, stream)
 
-    def decrypt(self, s: Scores, stream=None) -> torch.Tensor:
+    def decrypt(self, s: Scores, stream=None, with_error: bool = False):
+        """Decrypted numerators [n_cols][n_db] (device int64); with_error=True also returns the
+        largest pre-rounding distance |x - round(x)| (device fp32, numerator units)."""
         n = s.shape[1] * s.db.n_real
         out = torch.empty(max(n, 1), dtype=torch.int64, device=self.device)
-        C.icm_decrypt_scores(self.ctx, s.handle, out, n, stream)
-        return out[:n].view(s.shape[1], s.db.n_real)
+        if not with_error:
+            C.icm_decrypt_scores(self.ctx, s.handle, out, n, stream)
+            return out[:n].view(s.shape[1], s.db.n_real)
+        err = torch.empty(1, dtype=torch.float32, device=self.device)
+        C.icm_decrypt_scores_max_error(self.ctx, s.handle, out, n, err, stream)
+        return out[:n].view(s.shape[1], s.db.n_real), err
 
 
 class Plan:
@@ -224,11 +230,16 @@ class Plan:
 class Server:
     """Serving loop over resident chunks (icm_server_*): submit one eye at a time, wait per ticket."""
 
-    def __init__(self, eng: Engine, dbs, form="f16_crt", max_eyes=32, window_us=2000, max_pending=0):
+    def __init__(self, eng: Engine, dbs, form="f16_crt", max_eyes=32, window_us=2000, max_pending=0,
+                 max_batches=0, ws_bytes=None):
+        """ws_bytes: device workspace (default: icm_server_device_bytes, max_batches full batches)."""
         f = C.FORMS[form] if isinstance(form, str) else form
         self.eng, self.dbs = eng, dbs
-        cfg = C.icm_server_cfg(max_eyes=max_eyes, window_us=window_us, form=f, max_pending=max_pending)
+        cfg = C.icm_server_cfg(max_eyes=max_eyes, window_us=window_us, form=f, max_pending=max_pending,
+                               max_batches=max_batches)
         nbytes = C.icm_server_device_bytes(eng.ctx, [d.handle for d in dbs], cfg)
+        if ws_bytes is not None:
+            nbytes = ws_bytes
         self.ws = _u8(nbytes, eng.device)
         torch.cuda.synchronize()
         self.handle = C.icm_server_create(eng.ctx, [d.handle for d in dbs], cfg, self.ws, nbytes)
@@ -250,6 +261,10 @@ class Server:
 
     def stats(self):
         return C.icm_server_stats(self.handle)
+
+    def memory(self):
+        """(pool bytes, bytes of one full batch, peak reserved bytes, peak batches in flight)"""
+        return C.icm_server_memory(self.handle)
 
     def close(self, timeout_ms: int = 600000):
         if self.handle is not None:
