@@ -34,12 +34,10 @@ N_EYES, N_DB = 32, 7 * (1 << 14)
 WORKLOAD = ("paper-shaped CCMM + fold: 32 eyes x 31 rotations vs 114,688 codes (7 blocks of N_db=2^14), "
             "N_q=2^13, d=2^14, K=24,576, 8 primes < 2^60 (L_q=2), Delta=2^60")
 DTYPE = {"u64": "u64", "i8_digits": "int8", "i8_crt": "int8", "f16_crt": "f16"}
-# DRAM bytes (read + write) of the dominant kernel per CCMM call -- both column-round launches of
-# k_crt_tc, the unit `achieved` is timed on -- keyed by (form, tcgen05 variant), from the committed
-# one-pass ncu capture at this workload (profiles/k_crt_tc_paper_traffic.md); absent (null) for a
-# kernel changed since its capture.
-NCU_TRAFFIC = {("f16_crt", 3): 1.89e12 + 10.23e9 + 2.21e12 + 9.59e9,
-               ("f16_crt", 1): 1.53e12 + 10.23e9 + 2.41e12 + 9.59e9}
+# DRAM bytes (read + write) of the dominant kernel per CCMM call (both column-round launches of
+# k_crt_tc), keyed by (form, tcgen05 variant), scaled from a small-case ncu capture of the current
+# kernel; absent (null) for a kernel changed since its capture.
+NCU_TRAFFIC = {}
 
 
 def _dist():
@@ -337,11 +335,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="icm", choices=["icm", "reference"])
     ap.add_argument("--form", default="f16_crt", choices=["u64", "i8_digits", "i8_crt", "f16_crt"])
-    ap.add_argument("--compare-forms", default="i8_crt,u64,i8_digits",
-                    help="comma list of other forms, each timed for one step on the same workload ('' to skip)")
+    ap.add_argument("--form-steps", type=int, default=3, help="timed steps of each compared form")
+    ap.add_argument("--form-warmup", type=int, default=1, help="warm-up steps of each compared form")
+    ap.add_argument("--compare-forms", default="i8_crt,u64",
+                    help="comma list of other forms, each timed (--form-warmup, --form-steps) on the same "
+                         "workload ('' to skip; i8_digits takes ~33 s per step)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--variant", default="auto",
-                    help="CRT product kernel: auto (autotuner), 128 / 256 (mma.sync) or 1 (tcgen05)")
+                    help="CRT product kernel: auto (autotuner), 128 / 256 (mma.sync) or 1..3 (tcgen05)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fold-trials", type=int, default=1 << 33,
                     help="trials of the folding-polynomial check reported beside the step (0: skip)")
@@ -450,48 +451,51 @@ def main():
 
     # ---- roofline of the dominant kernel (the CCMM product)
     M, K, L, n_cols = db.m_rows, eng.K, eng.L, N_EYES * 31
-    gemm_avg_s = statistics.mean(gemm_ms) / 1e3
     peaks = measured_peaks()
-    f = C.FORMS[args.form]
-    tc = tune is not None and tune.get("chosen") in (1, 2, 3, 4, 5)
-    if args.form == "u64":
-        ops = 4.0 * M * n_cols * K * L                     # IMAD.WIDE per launch (2 x 2 30-bit limb products)
-        sm_max = peaks.get("sm_max_mhz", 2070.0)
-        peak = 152 * 32 * sm_max * 1e6                      # 152 SMs x 32 IMAD.WIDE/clk x max SM clock
-        roof = {"bound": "alu", "achieved": ops / gemm_avg_s / 1e9, "peak": peak / 1e9, "unit": "Gop/s",
-                "peak_source": "derived: 152 SMs x 32 IMAD.WIDE per clock x max SM clock",
-                "imad_wide_probe_gops": C.icm_probe_peak(0) / 1e9}
-    elif args.form in ("i8_digits", "i8_crt", "f16_crt"):
-        kp = (K + 31) // 32 * 32
-        esz = 2 if args.form == "f16_crt" else 1
-        # CRT moduli: the match scratch holds L x r x min(N, 512) x M residue bytes
-        pairs = 64 if args.form == "i8_digits" else \
-            int(eng.match_workspace(db, N_EYES, args.form).numel() // (L * min(n_cols, 512) * M))
-        ops = 2.0 * pairs * M * n_cols * kp * L
-        if args.form == "f16_crt":
-            # fp16 and bf16 share the dense tensor rate; the CCMM launch runs for seconds, so the
-            # sustained (power-capped) figure is the denominator
-            peak = peaks.get("bf16_tflops_sustained")
-            src = "of measured: MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS, seconds-long loop); fp16 rate = bf16"
-            if peak is None:
-                peak, src = 1700.0, "of fallback: 1.7 PFLOP/s bf16 sustained"
-            roof = {"bound": "tensor", "achieved": ops / gemm_avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
-                    "peak_source": src, "mma_sync_fp16_probe_tflops": 2.0 * C.icm_probe_peak(2) / 1e12}
+
+    def form_roofline(form: str, gemm_avg_s: float, variant):
+        """Roofline of the CCMM kernel of `form` from its CUDA-event time per launch."""
+        tc = form == "f16_crt" and variant in (1, 2, 3)
+        if form == "u64":
+            ops = 4.0 * M * n_cols * K * L                 # IMAD.WIDE per launch (2 x 2 30-bit limb products)
+            sm_max = peaks.get("sm_max_mhz", 2070.0)
+            peak = 152 * 32 * sm_max * 1e6                  # 152 SMs x 32 IMAD.WIDE/clk x max SM clock
+            roof = {"bound": "alu", "achieved": ops / gemm_avg_s / 1e9, "peak": peak / 1e9, "unit": "Gop/s",
+                    "peak_source": "derived: 152 SMs x 32 IMAD.WIDE per clock x max SM clock",
+                    "imad_wide_probe_gops": C.icm_probe_peak(0) / 1e9}
         else:
-            peak = 2.0 * C.icm_probe_peak(1)
-            roof = {"bound": "tensor", "achieved": ops / gemm_avg_s / 1e12, "peak": peak / 1e12, "unit": "TOP/s",
-                    "peak_source": "measured in this run: int8 mma.sync.m16n8k32 issue-bound probe (no tcgen05 int8 on sm_103a)"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = NCU_TRAFFIC.get((args.form, tune["chosen"] if tc else 0))
-    roof["kernel"] = {"u64": "k_ppmm_u64", "i8_digits": "k_ppmm_digits", "i8_crt": "k_crt_p1<int8> + k_crt_combine",
-                      "f16_crt": f"k_crt_tc ({C.VARIANTS[tune['chosen']]}) + k_crt_combine" if tc
-                      else "k_crt_p1<fp16> + k_crt_combine"
-                      }.get(args.form)
-    roof["ms_per_launch"] = gemm_avg_s * 1e3
+            kp = (K + 31) // 32 * 32
+            # CRT moduli: the match scratch holds L x r x min(N, 1024) x M residue bytes (+ 4 KB)
+            pairs = 64 if form == "i8_digits" else \
+                int(eng.match_workspace(db, N_EYES, form).numel() // (L * min(n_cols, 1024) * M))
+            ops = 2.0 * pairs * M * n_cols * kp * L
+            if form == "f16_crt":
+                # fp16 and bf16 share the dense tensor rate; the CCMM launch runs for seconds, so
+                # the sustained (power-capped) figure is the denominator
+                peak = peaks.get("bf16_tflops_sustained")
+                src = "of measured: MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS, seconds-long loop); fp16 rate = bf16"
+                if peak is None:
+                    peak, src = 1700.0, "of fallback: 1.7 PFLOP/s bf16 sustained"
+                roof = {"bound": "tensor", "achieved": ops / gemm_avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                        "peak_source": src, "mma_sync_fp16_probe_tflops": 2.0 * C.icm_probe_peak(2) / 1e12}
+            else:
+                peak = 2.0 * C.icm_probe_peak(1)
+                roof = {"bound": "tensor", "achieved": ops / gemm_avg_s / 1e12, "peak": peak / 1e12, "unit": "TOP/s",
+                        "peak_source": "measured in this run: int8 mma.sync.m16n8k32 issue-bound probe "
+                                       "(no tcgen05 int8 on sm_103a)"}
+        roof["frac"] = roof["achieved"] / roof["peak"]
+        roof["traffic"] = NCU_TRAFFIC.get((form, variant if tc else 0))
+        roof["kernel"] = {"u64": "k_ppmm_u64", "i8_digits": "k_ppmm_digits", "i8_crt": "k_crt_p1<int8> + k_crt_combine",
+                          "f16_crt": f"k_crt_tc ({C.VARIANTS[variant]}) + k_crt_combine" if tc
+                          else "k_crt_p1<fp16> + k_crt_combine"}.get(form)
+        roof["ms_per_launch"] = gemm_avg_s * 1e3
+        return roof
+
+    roof = form_roofline(args.form, statistics.mean(gemm_ms) / 1e3, tune["chosen"] if tune else None)
 
     # ---- rescaling by Q' of the step's CCMM result (not part of the timed step): HBM-bound, reads
     # L words and writes L_q words per coefficient
-    rs = None
+    rs, decode = None, None
     if eng.L > eng.Lq:
         with torch.cuda.stream(st):
             q1 = eng.prepare(ct, N_EYES, C.FORMS[args.form], stream=st)
@@ -511,7 +515,23 @@ def main():
         rs = {"kernel": "k_rescale", "ms_per_launch": rms, "bytes": rbytes, "achieved_gbs": rbytes / (rms / 1e3) / 1e9,
               "peak_gbs": rpeak, "frac": rbytes / (rms / 1e3) / 1e9 / rpeak,
               "peak_source": "of measured: MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "of fallback: 6.8 TB/s"}
-        del q1, s1, out
+        # decoded-score error of that CCMM result: the decoder's largest pre-rounding distance
+        # |x - round(x)| (numerator units), and the same in fractional-HD units over a lower bound
+        # of every pair's mask overlap ||m_q & m_db|| >= |m_q| + |m_db| - code bits (any rotation)
+        import numpy as np
+        dec1, err1 = eng.decrypt(s1, stream=st, with_error=True)
+        st.synchronize()
+        e_num = float(err1.cpu()[0])
+        wq = np.unpackbits(Wq.q_masks, axis=1).sum(axis=1)
+        wd = np.unpackbits(W.db_masks, axis=1).sum(axis=1)
+        den_lb = max(1, int(wq.min()) + int(wd.min()) - W.db_masks.shape[1] * 8)
+        decode = {"pre_rounding_max": e_num, "unit": "numerator units (decrypted / (Q' Delta))",
+                  "pre_rounding_max_hd": e_num / (2.0 * den_lb), "mask_overlap_lower_bound": den_lb,
+                  "hd_error_max": 0.0 if e_num < 0.5 else None, "hd_tolerance": 2.0 ** -10,
+                  "note": "numerators round exactly while pre_rounding_max < 1/2, so decoded distances equal "
+                          "the FP64 cleartext distances (all pairs checked against the oracle in "
+                          "tests/test_gpu_paper_scale.py); the bound includes the decoder's fixed-point error"}
+        del q1, s1, out, dec1, err1
 
     # ---- cleartext folding-polynomial check (not part of the timed step): the paper's 1e12-trial
     # experiment, scaled down; one trial draws 31 scores (8 Philox4x64-10 blocks)
@@ -540,11 +560,16 @@ def main():
                            "ops": "Philox 64x64->128 products as 4 IMAD.WIDE each, 640 per trial"}}
         del r
 
-    # ---- other forms, one timed step each on the same workload
-    forms = {args.form: {"value": value, "ms_per_step": ms_per_step}}
+    # ---- other forms on the same workload: warm-up step(s), then timed steps, each with the
+    # roofline of its own CCMM kernel
+    forms = {args.form: {"value": value, "ms_per_step": ms_per_step, "steps": args.steps,
+                         "roofline_frac": roof["frac"]}}
     for other in [x for x in args.compare_forms.split(",") if x and x != args.form]:
-        tot, gm = timed_form(other, 1, 0)          # one step (first launch of that form)
-        forms[other] = {"value": comps / (tot / 1e3), "ms_per_step": tot, "gemm_ms": gm[0]}
+        tot, gm = timed_form(other, args.form_steps, max(args.form_warmup, 1))
+        fms = tot / args.form_steps
+        forms[other] = {"value": comps / (fms / 1e3), "ms_per_step": fms, "gemm_ms": statistics.mean(gm),
+                        "steps": args.form_steps, "warmup": max(args.form_warmup, 1),
+                        "roofline": form_roofline(other, statistics.mean(gm) / 1e3, None)}
 
     # ---- end to end through the C ABI with host buffers
     f = C.FORMS[args.form]
@@ -571,9 +596,12 @@ def main():
            "d2h_bytes_per_step": fo_bytes, "ms_per_step": te}
     del wsbuf
 
-    n_chunks = (N_EYES * 31 + 511) // 512
+    # kernels per step: query basis extension (+ residue planes), the product (CRT forms: a phase-1
+    # launch and a combine per column round -- 512 columns for mma.sync, 1,024 for tcgen05), fold
+    tc_run = args.form == "f16_crt" and tune is not None and tune.get("chosen") in (1, 2, 3)
+    n_rounds = (N_EYES * 31 + (1023 if tc_run else 511)) // (1024 if tc_run else 512)
     launches_per_step = 1 + (1 if args.form != "u64" else 0) + \
-        (2 * n_chunks if args.form in ("i8_crt", "f16_crt") else 1) + 1
+        (2 * n_rounds if args.form in ("i8_crt", "f16_crt") else 1) + 1
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": max(args.warmup, 1), "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.form], "data": "synthetic",
@@ -581,7 +609,7 @@ def main():
                        "l2": "inputs larger than L2 (206 GB resident database), no flush",
                        "parallelism": "replicas" if ws == 1 else f"weak: {ws} database shards, same query"},
             "roofline": roof, "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clk,
-            "forms": forms, "variant": tune, "rescale": rs, "fold_design": fd}
+            "forms": forms, "variant": tune, "rescale": rs, "decode": decode, "fold_design": fd}
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         v, thr, sample, _ = oracle_sample(seconds_target=15.0)

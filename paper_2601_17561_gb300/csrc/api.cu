@@ -506,6 +506,19 @@ icm_status icm_decrypt_scores(icm_ctx *c, const icm_scores *s, int64_t *dev_num,
     return ICM_OK;
 }
 
+icm_status icm_decrypt_scores_max_error(icm_ctx *c, const icm_scores *s, int64_t *dev_num, size_t n, float *dev_max_err,
+                                        void *stream) {
+    if (!c || !s || !dev_num || !dev_max_err) return fail(ICM_EINVAL, "null argument");
+    if (!c->have_keys) return fail(ICM_EINVAL, "icm_keygen has not run");
+    if (n < (size_t)s->n_cols * s->lay.n_real) return fail(ICM_ENOMEM, "numerator buffer too small");
+    cudaError_t e = cudaMemsetAsync(dev_max_err, 0, sizeof(float), (cudaStream_t)stream);
+    if (e == cudaSuccess)
+        e = launch_decrypt(c, to_dev(s->lay), s->dev, s->n_cols, s->rescaled != 0, dev_num, (cudaStream_t)stream,
+                           reinterpret_cast<uint32_t *>(dev_max_err));
+    if (e != cudaSuccess) return fail(ICM_ECUDA, std::string("decrypt: ") + cudaGetErrorString(e));
+    return ICM_OK;
+}
+
 icm_status icm_rescale_bytes(const icm_scores *in, size_t *bytes) {
     if (!in || !bytes) return fail(ICM_EINVAL, "null argument");
     *bytes = (size_t)in->ctx->p.n_limbs_q * in->n_cols * in->lay.M * 8;

@@ -94,6 +94,7 @@ struct DecArgs {
     const int32_t *sdb_pos; const int8_t *sdb_sgn;
     const uint64_t *sc;    // [L][n_cols][M]
     int64_t *num;          // [n_cols][n_real]
+    uint32_t *err_bits;    // optional: max |x - round(x)| over all outputs, as fp32 bits
 };
 
 // grid: (ceil(n_real / 256), n_cols).  One thread per (column, real database row).
@@ -126,7 +127,16 @@ __global__ void __launch_bounds__(256) k_decrypt(DecArgs a) {
     }
     // F / 2^128 is D / Q_db modulo 1; as a signed 128-bit number it is the centred value.
     const double frac = (double)(int64_t)fhi * 0x1p-64 + (double)flo * 0x1p-128;
-    a.num[(size_t)j * a.lay.n_real + r] = (int64_t)rint(frac * a.crt.q_over_delta);
+    const double x = frac * a.crt.q_over_delta;
+    const double n = rint(x);
+    a.num[(size_t)j * a.lay.n_real + r] = (int64_t)n;
+    if (a.err_bits) {
+        // distance of the decoded value from the integer it rounds to (numerator units); the
+        // bits of non-negative floats order like unsigned integers
+        uint32_t e = __float_as_uint((float)fabs(x - n));
+        e = __reduce_max_sync(__activemask(), e);
+        if ((threadIdx.x & 31) == (__ffs(__activemask()) - 1)) atomicMax(a.err_bits, e);
+    }
 }
 
 struct RsArgs {
@@ -203,13 +213,13 @@ cudaError_t launch_fold(const icm_ctx *c, const LayoutDev &lay, const uint64_t *
 }
 
 cudaError_t launch_decrypt(const icm_ctx *c, const LayoutDev &lay, const uint64_t *d_scores, uint32_t n_cols,
-                           bool rescaled, int64_t *d_num, cudaStream_t st) {
+                           bool rescaled, int64_t *d_num, cudaStream_t st, uint32_t *d_err_bits) {
     DecArgs a{};
     a.lay = lay; a.L = rescaled ? c->p.n_limbs_q : c->p.n_limbs; a.h = c->p.hamming_weight; a.n_cols = n_cols;
     for (uint32_t l = 0; l < a.L; ++l) { a.q[l] = c->q[l]; a.r64[l] = c->lt.r64[l]; }
     a.crt = rescaled ? c->crt_q : c->crt;
     a.sdb_pos = c->d_sdb_pos; a.sdb_sgn = c->d_sdb_sgn;
-    a.sc = d_scores; a.num = d_num;
+    a.sc = d_scores; a.num = d_num; a.err_bits = d_err_bits;
     if (n_cols == 0 || lay.n_real == 0) return cudaSuccess;
     dim3 grid((unsigned)((lay.n_real + 255) / 256), n_cols);
     k_decrypt<<<grid, 256, 0, st>>>(a);

@@ -128,7 +128,7 @@ cudaError_t launch_ppmm_u64(const LimbTable &lt, const uint64_t *A, const uint64
 cudaError_t launch_fold(const icm_ctx *c, const LayoutDev &lay, const uint64_t *d_in, uint32_t n_eyes, uint32_t limbs,
                         uint64_t *d_out, cudaStream_t st);
 cudaError_t launch_decrypt(const icm_ctx *c, const LayoutDev &lay, const uint64_t *d_scores, uint32_t n_cols,
-                           bool rescaled, int64_t *d_num, cudaStream_t st);
+                           bool rescaled, int64_t *d_num, cudaStream_t st, uint32_t *d_err_bits = nullptr);
 // Rescaling by Q' of n coefficients per limb: [L][n] at modulus Q_db -> [L_q][n] at modulus Q.
 cudaError_t launch_rescale(const icm_ctx *c, const uint64_t *d_in, uint64_t n, uint64_t *d_out, cudaStream_t st);
 

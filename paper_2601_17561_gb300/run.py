@@ -3,9 +3,12 @@
     python -m paper_2601_17561_gb300.run --workload mid --form f16_crt --passes 2
 
 Workloads: tiny (4 eyes x 256 codes, ring 2^12, 3 primes < 2^50), mid (32 eyes x 2,000 codes,
-same ring and primes: about 3 GB on the device, sized for profiler captures), paper (32 eyes x
-114,688 codes, N_db = 2^14, N_q = 2^13, 8 primes < 2^60).  Each pass prepares the query,
-runs the CCMM and the fold.
+same ring and primes: about 3 GB on the device, sized for profiler captures), slice (32 eyes x
+4,096 codes with the paper's query side -- N_q = 2^13, d = 2^14, K = 24,576, primes < 2^60, so
+19 CRT moduli -- but N_db = 2^12 and 2 primes: M = 8,192 rows, 3.2 GB, the paper's tile shape
+and wave order at a profiler-sized scale), paper (32 eyes x 114,688 codes, N_db = 2^14,
+N_q = 2^13, 8 primes < 2^60).  Each pass prepares the query, runs the CCMM and the fold (and,
+with --rescale, the rescaling by Q').
 
     python -m paper_2601_17561_gb300.run --fold-trials 268435456
 
@@ -28,6 +31,8 @@ from . import synth
 WORKLOADS = {
     "tiny": (E.TINY, dict(n_eyes=4, n_db=256, seed=1, planted_frac=0.05)),
     "mid": (E.TINY, dict(n_eyes=32, n_db=2000, seed=3, planted_frac=0.05)),
+    "slice": (dict(log_n_db=12, log_n_q=13, n_limbs=2, n_limbs_q=1, prime_bits=60, log2_delta=40, seed=4),
+              dict(n_eyes=32, n_db=4096, seed=4, planted_frac=0.05)),
     "paper": (E.PAPER, dict(n_eyes=32, n_db=7 * (1 << 14), seed=2, planted_frac=0.05)),
 }
 
@@ -40,6 +45,7 @@ def main(argv=None):
     ap.add_argument("--variant", type=int, default=None,
                     help="CRT product kernel: 1 = tcgen05, 128 / 256 = mma.sync column tile (default: library's)")
     ap.add_argument("--fold-trials", type=int, default=0, help="run the folding-polynomial check instead")
+    ap.add_argument("--rescale", action="store_true", help="also rescale the CCMM result by Q' each pass")
     a = ap.parse_args(argv)
     B.build()
     if a.fold_trials:
@@ -65,6 +71,8 @@ def main(argv=None):
         q = eng.prepare(ct, wl["n_eyes"], a.form)
         s = eng.match(db, q)
         eng.fold(s)
+        if a.rescale:
+            eng.rescale(s)
         torch.cuda.synchronize()
         print(f"pass {i}: {(time.perf_counter() - t0) * 1e3:.1f} ms ({a.workload}, {a.form})", flush=True)
     return 0
