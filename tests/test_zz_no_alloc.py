@@ -35,13 +35,15 @@ def test_noalloc_matches_ppmm_twice(form):
 
 
 def test_noalloc_rejects_oversize():
-    """A workspace above the 64 MiB static array is refused with ICM_ENOMEM (host-side check, no
-    device work), and non-CRT forms are unsupported."""
+    """A workspace above the 64 MiB static array is refused with ICM_ENOMEM (host-side check made
+    before the pointer checks, so the null pointers passed here can never reach a kernel: if the
+    size check regressed, the call would fail with ICM_EINVAL on the host instead), and non-CRT
+    forms are unsupported."""
     B.build()
     q = O.primes(60, 2)
     with pytest.raises(C.IcmError) as e:
-        C.icm_ppmm_noalloc(C.ICM_FORM_F16_CRT, q, 2, 1, 1, 1, 100000, 992, 24576, stream=0)
+        C.icm_ppmm_noalloc(C.ICM_FORM_F16_CRT, q, 2, None, None, None, 100000, 992, 24576, stream=0)
     assert e.value.status == C.ICM_ENOMEM
     with pytest.raises(C.IcmError) as e:
-        C.icm_ppmm_noalloc(C.ICM_FORM_U64, q, 2, 1, 1, 1, 10, 10, 10, stream=0)
+        C.icm_ppmm_noalloc(C.ICM_FORM_U64, q, 2, None, None, None, 10, 10, 10, stream=0)
     assert e.value.status == C.ICM_EUNSUPPORTED
