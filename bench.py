@@ -34,10 +34,18 @@ N_EYES, N_DB = 32, 7 * (1 << 14)
 WORKLOAD = ("paper-shaped CCMM + fold: 32 eyes x 31 rotations vs 114,688 codes (7 blocks of N_db=2^14), "
             "N_q=2^13, d=2^14, K=24,576, 8 primes < 2^60 (L_q=2), Delta=2^60")
 DTYPE = {"u64": "u64", "i8_digits": "int8", "i8_crt": "int8", "f16_crt": "f16"}
-# DRAM bytes (read + write) of the dominant kernel per CCMM call (both column-round launches of
-# k_crt_tc), keyed by (form, tcgen05 variant), scaled from a small-case ncu capture of the current
-# kernel; absent (null) for a kernel changed since its capture.
-NCU_TRAFFIC = {}
+# DRAM bytes (read + write) of the dominant kernel per CCMM call, keyed by (form, tcgen05
+# variant), from one-pass ncu captures of the current kernels on the 8,192-row slice of this shape
+# (2 limbs) scaled by 64 (16x the row tiles, 4x the limbs: the traffic of a wave of co-resident
+# tiles does not depend on M, and the waves grow with row tiles x limbs x rounds); the int8 CRT
+# figure scales one 512-column round by 2 rounds.  Absent (null) for a kernel changed since.
+NCU_TRAFFIC = {
+    ("f16_crt", 1): 64 * (21_816_439_808 + 309_587_200),
+    ("f16_crt", 2): 64 * (22_078_293_504 + 310_923_520),
+    ("f16_crt", 3): 64 * (61_499_651_072 + 394_573_824),
+    ("i8_crt", 0): 2 * 64 * (12_206_364_000 + 161_416_192),
+    ("u64", 0): 64 * (96_624_647_000 + 141_553_920),
+}
 
 
 def _dist():
@@ -215,12 +223,16 @@ def run_batching(args, dev):
 
 def run_serving(args, dev):
     """Serving form: a resident encrypted database of 2^17 codes (8 primes), query eyes submitted
-    one by one at Poisson rates; the request loop batches up to 32 eyes per launch.  Reports
-    eyes/s and p50/p99 latency (submission to result) per rate; checks sampled results bit-exact
-    against the direct (non-serving) path."""
+    one by one at Poisson rates; the request loop admits them by free device memory, batches up to
+    32 eyes per launch and overlaps consecutive batches (two batch slots where the memory left
+    beside the database holds two full batches).  Each rate submits for --seconds or until
+    --serving-eyes eyes, whichever comes first, then drains.  Reports eyes/s and p50/p99 latency
+    (submission to result) per rate; checks sampled results bit-exact against the direct
+    (non-serving) path."""
     import numpy as np
     import torch
     from paper_2601_17561_gb300 import engine as E
+    from paper_2601_17561_gb300 import icm as C
     from paper_2601_17561_gb300 import synth
     n_db = 1 << 17
     pool = 64
@@ -229,48 +241,66 @@ def run_serving(args, dev):
     db = eng.encrypt_db(W.db_codes, W.db_masks)
     ct = eng.encrypt_query(W.q_codes, W.q_masks, W.eye_ids)
     torch.cuda.synchronize()
+    best = None
     if args.form in ("i8_crt", "f16_crt"):
         qt = eng.prepare(eng.encrypt_query(W.q_codes[:32], W.q_masks[:32], W.eye_ids[:32]), 32, args.form)
         best, _ = eng.autotune([db], qt)
         del qt
         torch.cuda.empty_cache()
-    srv = E.Server(eng, [db], form=args.form, max_eyes=32, window_us=args.window_us)
-    cts = srv.eye_cts(ct, pool)
-    # reference for two sampled eyes through the direct path
+    # reference for two sampled eyes through the direct path (before the server takes its pool)
     refs = {}
     for e in (0, pool - 1):
         cte = eng.encrypt_query(W.q_codes[e:e + 1], W.q_masks[e:e + 1], W.eye_ids[e:e + 1])
         qq = eng.prepare(cte, 1, args.form)
         refs[e] = eng.fold(eng.match(db, qq)).residues().reshape(-1)
+        del qq, cte
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    cfg1 = C.icm_server_cfg(max_eyes=32, window_us=args.window_us, form=C.FORMS[args.form], max_batches=1)
+    full = C.icm_server_device_bytes(eng.ctx, [db.handle], cfg1)
+    free = torch.cuda.mem_get_info(dev)[0]
+    margin = 4 << 30
+    ws_bytes = min(2 * full, max(full, free - margin))
+    srv = E.Server(eng, [db], form=args.form, max_eyes=32, window_us=args.window_us, ws_bytes=ws_bytes)
+    cts = srv.eye_cts(ct, pool)
     rng = np.random.default_rng(5)
     rates = [float(x) for x in args.rates.split(",")]
     results = {}
     ok = True
     for lam in rates:
+        b0 = srv.stats()
         outs, tickets = [], []
         t0 = time.perf_counter()
         n = 0
-        while time.perf_counter() - t0 < args.seconds:
+        while time.perf_counter() - t0 < args.seconds and n < args.serving_eyes:
             e = n % pool
             o = np.zeros(srv.out_words, np.uint64)
             tickets.append((e, srv.submit(cts[e], o)))
             outs.append(o)
             n += 1
             time.sleep(float(rng.exponential(1.0 / lam)))
+        t_sub = time.perf_counter() - t0
         lat = [srv.wait(t) for _, t in tickets]
         wall = time.perf_counter() - t0
         for (e, _), o in zip(tickets, outs):
             if e in refs and not np.array_equal(o, refs[e]):
                 ok = False
+        b1 = srv.stats()
         lat = np.array(lat)
-        results[str(lam)] = {"eyes": n, "eyes_per_s": n / wall, "p50_ms": float(np.percentile(lat, 50)),
-                             "p99_ms": float(np.percentile(lat, 99)), "mean_batch": srv.stats()[2]}
+        results[str(lam)] = {"eyes": n, "offered_eyes_per_s": n / t_sub, "eyes_per_s": n / wall,
+                             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                             "batches": int(b1[1] - b0[1]), "mean_batch": n / max(1, int(b1[1] - b0[1]))}
+    pool_bytes, full_bytes, peak_bytes, peak_batches = srv.memory()
     srv.close()
+    sat = max(r["eyes_per_s"] for r in results.values())
     line = {"metric": "serving form: p50/p99 latency and eyes/s at Poisson arrival rates", "unit": "ms",
             "n_gpus": 1, "data": "synthetic", "dtype": DTYPE[args.form],
             "config": {"workload": "resident database of 2^17 codes (M = 147,456), 8 primes < 2^60; "
-                       f"<= 32 eyes per launch, window {args.window_us} us, {args.seconds} s per rate",
-                       "form": args.form}, "rates": results, "sampled_results_bit_exact": ok}
+                       f"<= 32 eyes per launch, window {args.window_us} us, up to {args.seconds} s or "
+                       f"{args.serving_eyes} eyes per rate", "form": args.form, "variant": best},
+            "memory": {"pool_bytes": pool_bytes, "full_batch_bytes": full_bytes, "peak_reserved_bytes": peak_bytes,
+                       "peak_batches_in_flight": peak_batches},
+            "rates": results, "max_served_eyes_per_s": sat, "sampled_results_bit_exact": ok}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -350,8 +380,9 @@ def main():
                     help="paper: the headline CCMM step; batching / serving: the query-batching and "
                          "request-loop forms; p2: the paper's p^2 modulus family on one CCMM slice "
                          "(one JSON line each, not the headline)")
-    ap.add_argument("--rates", default="2,4,8", help="serving: Poisson arrival rates (eyes/s)")
-    ap.add_argument("--seconds", type=float, default=20.0, help="serving: submission time per rate")
+    ap.add_argument("--rates", default="16,32,64,128,256,512", help="serving: Poisson arrival rates (eyes/s)")
+    ap.add_argument("--seconds", type=float, default=20.0, help="serving: longest submission time per rate")
+    ap.add_argument("--serving-eyes", type=int, default=320, help="serving: most eyes submitted per rate")
     ap.add_argument("--window-us", type=int, default=20000, help="serving: batching window")
     args = ap.parse_args()
     ws, rank, local = _dist()
@@ -465,9 +496,8 @@ def main():
                     "imad_wide_probe_gops": C.icm_probe_peak(0) / 1e9}
         else:
             kp = (K + 31) // 32 * 32
-            # CRT moduli: the match scratch holds L x r x min(N, 1024) x M residue bytes (+ 4 KB)
-            pairs = 64 if form == "i8_digits" else \
-                int(eng.match_workspace(db, N_EYES, form).numel() // (L * min(n_cols, 1024) * M))
+            # products per modular MAC: 64 digit pairs, or one per CRT modulus
+            pairs = 64 if form == "i8_digits" else len(C.icm_ctx_crt_moduli(eng.ctx))
             ops = 2.0 * pairs * M * n_cols * kp * L
             if form == "f16_crt":
                 # fp16 and bf16 share the dense tensor rate; the CCMM launch runs for seconds, so
@@ -485,6 +515,9 @@ def main():
                                        "(no tcgen05 int8 on sm_103a)"}
         roof["frac"] = roof["achieved"] / roof["peak"]
         roof["traffic"] = NCU_TRAFFIC.get((form, variant if tc else 0))
+        if roof["traffic"] is not None:
+            roof["traffic_note"] = ("DRAM bytes per CCMM call: one-pass ncu capture on the 8,192-row slice of "
+                                    "this shape, scaled x64 (profiles/)")
         roof["kernel"] = {"u64": "k_ppmm_u64", "i8_digits": "k_ppmm_digits", "i8_crt": "k_crt_p1<int8> + k_crt_combine",
                           "f16_crt": f"k_crt_tc ({C.VARIANTS[variant]}) + k_crt_combine" if tc
                           else "k_crt_p1<fp16> + k_crt_combine"}.get(form)

@@ -108,6 +108,11 @@ icm_status icm_ctx_create(const icm_params *p, icm_ctx **out);
 void icm_ctx_destroy(icm_ctx *ctx);
 /* Copy the primes (n >= n_limbs values) to host memory. */
 icm_status icm_ctx_primes(const icm_ctx *ctx, uint64_t *primes, size_t n);
+/* The small moduli of the CRT forms (Section 6.2.2's RNS of moduli below 2^8): *n_moduli receives
+ * their count r (the tensor-core products per modular multiply-add), and the first min(cap, r)
+ * moduli go to `moduli` (host array, may be NULL with cap 0).  ICM_EBOUND if the CRT forms are
+ * unavailable for this context's primes and K. */
+icm_status icm_ctx_crt_moduli(const icm_ctx *ctx, int32_t *moduli, size_t cap, size_t *n_moduli);
 
 /* Key generation (Section 2.2.2 refers to the CKKS paper): samples the database secrets
  * s_{db,t} (degree N_db) and query secrets s_{q,t} (degree N_q) as sparse ternary polynomials
@@ -235,14 +240,14 @@ icm_status icm_plan_create(icm_ctx *ctx, const icm_db *const *dbs, size_t n_dbs,
 icm_status icm_plan_launch(icm_plan *plan, void *stream);
 void icm_plan_destroy(icm_plan *plan);
 
-/* Kernel variant of the CRT forms' product: 0 or 256 = mma.sync with 256-column tiles (default),
- * 128 = mma.sync with 128-column tiles; for the fp16 form on a database in the storage form, the
- * tcgen05 kernel (tensor-memory accumulators, TMA-fed, one modulus on 512 columns per block and
- * round, every round of up to 1,024 columns in one launch; needs an even K, else variant 0 runs):
- * 1 = rings of 8 raw-database and 4 operand slots; 2 = the same with a wave bound between blocks
- * (a block starts fetching its next tile once every block has fetched its current one;
- * cooperative launch); 3 = 4 raw-database and 8 operand slots.  Results are identical; only
- * speed differs. */
+/* Kernel variant of the CRT forms' product: 256 = mma.sync with 256-column tiles, 128 = mma.sync
+ * with 128-column tiles; for the fp16 form on a database in the storage form, the tcgen05 kernel
+ * (tensor-memory accumulators, TMA-fed, one modulus on 512 columns per block and round, every
+ * round of up to 1,024 columns in one launch; needs an even K, else variant 256 runs): 1 = rings
+ * of 8 raw-database and 4 operand slots; 2 = the same with a wave bound between blocks (a block
+ * starts fetching its next tile once every block has fetched its current one; cooperative
+ * launch); 3 = 4 raw-database and 8 operand slots.  0 restores the default, variant 2 (which the
+ * int8 form and odd K run as 256).  Results are identical; only speed differs. */
 icm_status icm_ctx_set_variant(icm_ctx *ctx, int variant);
 /* Failure detection of the tcgen05 kernel (no counterpart in the paper).  Every device-side wait
  * of that kernel (barrier phases, the wave bound) gives up after wait_ns nanoseconds of

@@ -239,6 +239,14 @@ icm_status icm_ctx_primes(const icm_ctx *ctx, uint64_t *primes, size_t n) {
     return ICM_OK;
 }
 
+icm_status icm_ctx_crt_moduli(const icm_ctx *ctx, int32_t *moduli, size_t cap, size_t *n_moduli) {
+    if (!ctx || !n_moduli || (cap && !moduli)) return fail(ICM_EINVAL, "bad arguments");
+    if (!ctx->i8_crt_ok) return fail(ICM_EBOUND, "CRT forms unavailable for these primes / K");
+    *n_moduli = ctx->i8_crt.n_mod;
+    for (size_t i = 0; i < cap && i < ctx->i8_crt.n_mod; ++i) moduli[i] = ctx->i8_crt.mod[i];
+    return ICM_OK;
+}
+
 }  // extern "C"
 
 namespace icm {

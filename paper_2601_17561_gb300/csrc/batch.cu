@@ -199,7 +199,7 @@ icm_status icm_ctx_set_device_wait(icm_ctx *c, uint64_t wait_ns, int inject_stal
 icm_status icm_ctx_set_variant(icm_ctx *c, int variant) {
     if (!c || (variant != 0 && !crt_tc_variant(variant) && variant != 128 && variant != 256))
         return api_fail(ICM_EINVAL, "variant must be 0, 1..3, 128 or 256");
-    c->crt_bn = variant == 0 ? 256 : variant;
+    c->crt_bn = variant == 0 ? 2 : variant;
     return ICM_OK;
 }
 

@@ -56,7 +56,7 @@ struct icm_ctx {
     std::vector<uint64_t> delta_mods;
     icm::I8Consts i8_digits, i8_crt;    // constants of the int8 tensor-core forms for (q, K)
     bool i8_crt_ok = false;
-    int crt_bn = 256;                   // column tile of the CRT product kernel (tunable)
+    int crt_bn = 2;                     // CRT product variant: tcgen05 wave where it applies, else 256
     bool have_keys = false;
     int device = -1;
     // device copies of the secret supports: s_{db,t} for t < max_db_blocks, s_{q,t} for t < n_qblk

@@ -430,10 +430,44 @@ cudaError_t launch_crt_planes(bool f16, const I8Consts &k, const uint64_t *op, v
     return cudaGetLastError();
 }
 
+// The constants of limbs [l0, l0 + n) as a context of n limbs.
+static I8Consts limb_slice(const I8Consts &k, uint32_t l0, uint32_t n) {
+    I8Consts s = k;
+    s.n_limbs = n;
+    for (uint32_t l = 0; l < n; ++l) {
+        const uint32_t f = l0 + l;
+        s.q[l] = k.q[f]; s.r64[l] = k.r64[f];
+        for (int t = 0; t < 15; ++t) { s.pw8[l][t] = k.pw8[f][t]; s.pw8s[l][t] = k.pw8s[f][t]; }
+        for (uint32_t i = 0; i < ICM_MAX_MODULI; ++i) { s.W[l][i] = k.W[f][i]; s.Ws[l][i] = k.Ws[f][i]; }
+        s.Mq[l] = k.Mq[f]; s.Mqs[l] = k.Mqs[f];
+        s.pd[l] = k.pd[f]; s.inv_p[l] = k.inv_p[f];
+    }
+    return s;
+}
+
 cudaError_t launch_ppmm_crt_grouped(bool f16, int bn, const I8Consts &k, const ChunkTab &tab, const void *Bp, uint64_t N,
                                     uint64_t K, uint64_t Kp, void *scratch, cudaStream_t st) {
     const uint64_t Mall = tab.row0[tab.n];
     if (Mall == 0 || N == 0) return cudaSuccess;
+    // limbs in groups that fit the residue scratch: each group is the same product on a slice of
+    // the database words, query planes and outputs
+    const uint32_t G = crt_limb_group(k.n_limbs, k.n_mod, N, Mall);
+    if (G < k.n_limbs) {
+        const uint64_t plane_limb = crt_plane_bytes(f16, 1, k.n_mod, N, Kp);
+        for (uint32_t l0 = 0; l0 < k.n_limbs; l0 += G) {
+            const uint32_t n = std::min(G, k.n_limbs - l0);
+            ChunkTab t = tab;
+            for (uint32_t c = 0; c < tab.n; ++c) {
+                t.A[c] = tab.A[c] + (uint64_t)l0 * tab.M[c] * K;
+                t.C[c] = tab.C[c] + (uint64_t)l0 * N * tab.M[c];
+            }
+            const I8Consts s = limb_slice(k, l0, n);
+            cudaError_t e = launch_ppmm_crt_grouped(f16, bn, s, t, static_cast<const char *>(Bp) + l0 * plane_limb, N,
+                                                    K, Kp, scratch, st);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
     if (f16 && crt_tc_variant(bn) && tab.a_digits && crt_tc_supported(K))
         return launch_ppmm_crt_tc(k, tab, Bp, N, K, Kp, scratch, bn, st);
     if (bn != 128) bn = 256;

@@ -91,12 +91,20 @@ __host__ __device__ __forceinline__ uint64_t crt_f16_off(uint64_t j, uint64_t k,
            (k & 7);
 }
 // small-modulus CRT forms (int8 or fp16 operands): query residue planes, two-phase product.
-// Scratch: the residue bytes [L][r][min(N, 1024)][M] (one column round of the largest kernel,
-// rounded up to 256 bytes), then CRT_PROGRESS_BYTES for the tcgen05 kernel's wave counter and
-// give-up word.
+// The limbs are processed in groups whose residue bytes stay within CRT_SCRATCH_CAP (at least one
+// limb per group).  Scratch: the residue bytes [G][r][min(N, 1024)][M] of one group of G limbs
+// and one column round of the largest kernel (rounded up to 256 bytes), then CRT_PROGRESS_BYTES
+// for the tcgen05 kernel's wave counter and give-up word.
 constexpr uint64_t CRT_PROGRESS_BYTES = 4096;
+constexpr uint64_t CRT_SCRATCH_CAP = 6ull << 30;
+inline uint32_t crt_limb_group(uint32_t n_limbs, uint32_t n_mod, uint64_t N, uint64_t M) {
+    const uint64_t per = (uint64_t)n_mod * (N < 1024 ? N : 1024) * M;
+    const uint64_t g = per ? CRT_SCRATCH_CAP / per : n_limbs;
+    return g < 1 ? 1u : (g > n_limbs ? n_limbs : (uint32_t)g);
+}
 inline uint64_t crt_scratch_main_bytes(uint32_t n_limbs, uint32_t n_mod, uint64_t N, uint64_t M) {
-    return ((uint64_t)n_limbs * n_mod * (N < 1024 ? N : 1024) * M + 255) / 256 * 256;
+    const uint64_t per = (uint64_t)n_mod * (N < 1024 ? N : 1024) * M;
+    return (crt_limb_group(n_limbs, n_mod, N, M) * per + 255) / 256 * 256;
 }
 uint64_t crt_scratch_bytes(uint32_t n_limbs, uint32_t n_mod, uint64_t N, uint64_t M);
 cudaError_t launch_crt_planes(bool f16, const I8Consts &k, const uint64_t *op, void *planes, uint64_t N, uint64_t K,

@@ -53,6 +53,7 @@ _SIGS = {
     "icm_ctx_create": (_i32, [ctypes.POINTER(icm_params), ctypes.POINTER(_vp)]),
     "icm_ctx_destroy": (None, [_vp]),
     "icm_ctx_primes": (_i32, [_vp, _vp, _sz]),
+    "icm_ctx_crt_moduli": (_i32, [_vp, _vp, _sz, ctypes.POINTER(_sz)]),
     "icm_keygen": (_i32, [_vp]),
     "icm_db_bytes": (_i32, [_vp, _sz, ctypes.POINTER(_sz), ctypes.POINTER(_sz)]),
     "icm_db_encrypt": (_i32, [_vp, _vp, _vp, _sz, _u64, _vp, _sz, _vp, ctypes.POINTER(_vp)]),
@@ -164,6 +165,15 @@ def icm_ctx_destroy(ctx):
 def icm_ctx_primes(ctx, n: int = 8):
     arr = (ctypes.c_uint64 * n)()
     _check(lib().icm_ctx_primes(ctx, arr, n), "icm_ctx_primes")
+    return list(arr)
+
+
+def icm_ctx_crt_moduli(ctx):
+    """The CRT forms' small moduli (list of ints)."""
+    n = _sz()
+    _check(lib().icm_ctx_crt_moduli(ctx, None, 0, ctypes.byref(n)), "icm_ctx_crt_moduli")
+    arr = (ctypes.c_int32 * n.value)()
+    _check(lib().icm_ctx_crt_moduli(ctx, arr, n.value, ctypes.byref(n)), "icm_ctx_crt_moduli")
     return list(arr)
 
 

@@ -54,6 +54,29 @@ def test_primes_agree_with_oracle_rule(lib, cfg):
     assert got == O.primes(cfg["prime_bits"], cfg["n_limbs"])
 
 
+@pytest.mark.parametrize("cfg", [O.TINY, O.PAPER])
+def test_crt_moduli_cover_the_product_range(lib, cfg):
+    """The CRT forms' small moduli: odd, below 2^8, pairwise coprime, and their product exceeds
+    twice the largest |sum of K centred residue products| (so the CRT value is the exact integer),
+    with at least 8 bits to spare."""
+    import math
+    ctx = C.icm_ctx_create(_params(**cfg))
+    try:
+        mods = C.icm_ctx_crt_moduli(ctx)
+        q = C.icm_ctx_primes(ctx, cfg["n_limbs"])
+    finally:
+        C.icm_ctx_destroy(ctx)
+    K = (1 << 14) + (1 << cfg["log_n_q"])
+    assert all(m % 2 == 1 and 3 <= m < 256 for m in mods)
+    assert all(math.gcd(a, b) == 1 for i, a in enumerate(mods) for b in mods[i + 1:])
+    bound = K * ((max(q) - 1) // 2) ** 2
+    assert math.prod(mods) > 2 * bound * 256
+    # greedy from 255 down: dropping the smallest modulus no longer covers the range with margin
+    assert math.prod(mods[:-1]) < 2 * (bound + 1) * 256 * 2
+    if cfg is O.PAPER:
+        assert len(mods) == 19
+
+
 def test_bounds_rejected(lib):
     # Delta too large: the message wraps modulo Q_db
     with pytest.raises(C.IcmError) as e:
