@@ -11,6 +11,9 @@ Heavy exact loops (encryption, the u128 schoolbook product, decryption sums, pop
 decoding and the fold, each written from the passage it cites.  Readings of passages where the
 paper is silent are listed beside the functions that take them.
 
+`slots.py` holds the slot-encoded database variant and the normalisation of the scores (Section
+2.2.1 Ecd_slot, Section 2.3, Algorithm 2), pinned by `tests/test_slot_pins.py`.
+
 Parity status: every function here is pinned by `tests/test_oracle_pins.py` (no function is
 "parity unpinned").
 """
@@ -76,6 +79,8 @@ def lib():
         _lib.orc_hd_counts.argtypes = [i32, i32, i32, vp, vp, vp, vp, vp, vp]
         _lib.orc_negacyclic_mul.restype = None
         _lib.orc_negacyclic_mul.argtypes = [vp, vp, i32, u64, vp]
+        _lib.orc_negacyclic_mulmod.restype = None
+        _lib.orc_negacyclic_mulmod.argtypes = [vp, vp, i32, u64, vp]
         _lib.orc_omp_threads.restype = i32
         _lib.orc_omp_threads.argtypes = []
     return _lib
@@ -337,16 +342,26 @@ def db_rows(P: Params, db_codes, db_masks, row_ids, chunk: int = 0) -> np.ndarra
     r >= number of templates, encrypt zero)."""
     row_ids = np.ascontiguousarray(np.asarray(row_ids, np.int64))
     n_tpl = db_codes.shape[0]
-    cp = np.zeros((len(row_ids), P.d2), np.int8)
+    cp = np.zeros((len(row_ids), P.d2), np.int32)
     sel = [(x, int(r) - P.ndb) for x, r in enumerate(row_ids) if r >= P.ndb and int(r) - P.ndb < n_tpl]
     if sel:
         idx = np.array([r for _, r in sel])
         cb, mb = unpack(db_codes[idx]), unpack(db_masks[idx])
         cp[[x for x, _ in sel]] = cprime(cb, mb, P.d2)
+    return db_rows_from_messages(P, cp, row_ids, chunk)
+
+
+def db_rows_from_messages(P: Params, msg: np.ndarray, row_ids, chunk: int = 0) -> np.ndarray:
+    """Selected rows of an encrypted database chunk (Section 6.2.1) whose message matrix rows are
+    given: msg [n_rows][d2] integers (|m| < 2^21) for the selected rows in row_ids order (rows of
+    a-part ids are ignored).  [L][n_rows][K]."""
+    row_ids = np.ascontiguousarray(np.asarray(row_ids, np.int64))
+    msg = np.ascontiguousarray(msg, np.int32)
+    assert msg.shape == (len(row_ids), P.d2)
     out = np.zeros((P.n_limbs, len(row_ids), P.K), np.uint64)
     q = np.array(P.q, np.uint64)
     rc = lib().orc_db_rows(P.n_limbs, P.n_limbs_q, _p(q), P.ndb, P.nq, P.d2, P.h, P.eta, P.seed, chunk,
-                           _p(row_ids), len(row_ids), _p(cp), _p(out))
+                           _p(row_ids), len(row_ids), _p(msg), _p(out))
     assert rc == 0
     return out
 
@@ -370,6 +385,16 @@ def negacyclic_mul(s: np.ndarray, a: np.ndarray, q: int) -> np.ndarray:
 
 
 # ------------------------------------------------------------------------------ CCMM / fold / decrypt
+
+def negacyclic_mulmod(a: np.ndarray, b: np.ndarray, q: int) -> np.ndarray:
+    """a * b in Z_q[X]/(X^N + 1) for residues a, b in [0, q) (Section 2.2.1 plaintext ring)."""
+    a = np.ascontiguousarray(a, np.uint64)
+    b = np.ascontiguousarray(b, np.uint64)
+    assert a.shape == b.shape and a.ndim == 1
+    out = np.zeros_like(a)
+    lib().orc_negacyclic_mulmod(_p(a), _p(b), len(a), q, _p(out))
+    return out
+
 
 def ppmm(q, A: np.ndarray, B: np.ndarray) -> np.ndarray:
     """C[l][j][i] = sum_k A[l][i][k] B[l][j][k] mod q_l (u128 schoolbook, Section 2.3)."""

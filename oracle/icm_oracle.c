@@ -119,6 +119,28 @@ void orc_negacyclic_mul(const int8_t *s, const uint64_t *a, int n, uint64_t q, u
     support_free(&sp);
 }
 
+/* Product of two polynomials of Z_q[X]/(X^n + 1) (Section 2.2.1 plaintext ring), schoolbook:
+ * out[k] = sum_{i + j = k} a_i b_j - sum_{i + j = k + n} a_i b_j  (mod q), inputs in [0, q), q < 2^62.
+ * The u128 partial sums are reduced every 16 products (16 * 2^124 = 2^128). */
+void orc_negacyclic_mulmod(const uint64_t *a, const uint64_t *b, int n, uint64_t q, uint64_t *out) {
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < n; ++k) {
+        u128 pos = 0, neg = 0;
+        int cnt = 0;
+        for (int i = 0; i <= k; ++i) {
+            pos += (u128)a[i] * b[k - i];
+            if (++cnt == 16) { pos %= q; cnt = 0; }
+        }
+        cnt = 0;
+        for (int i = k + 1; i < n; ++i) {
+            neg += (u128)a[i] * b[n + k - i];
+            if (++cnt == 16) { neg %= q; cnt = 0; }
+        }
+        const uint64_t p = (uint64_t)(pos % q), m = (uint64_t)(neg % q);
+        out[k] = p >= m ? p - m : p + q - m;
+    }
+}
+
 /* ---------------------------------------------------------------- encryption ---- */
 
 /* MSRLWE query encryption under S_q modulo Q = q_0 ... q_{Lq-1} (Section 2.3 shared-a format,
@@ -198,13 +220,16 @@ int orc_query_extend(int L, int Lq, const uint64_t *q, size_t n, const uint64_t 
  *   a-part row i < ndb:  [A1 A2][i][k] uniform mod Q_db (independent residues per limb);
  *   b-row r (block t = r / ndb, coefficient i = r % ndb):
  *        B[r][k] = -(s_{db,t} * A[:, k])[i] + Q' * W[r][k] + E[r][k]    (mod q_l)
- *   with W[r][k] = c'_r[k] for k < d2 and W[r][d2 + j] = (M_db S_q)[r][j].
+ *   with W[r][k] = m_r[k] for k < d2 and W[r][d2 + j] = (M_db S_q)[r][j], where m_r is row r
+ *   of the database message matrix: the masked bit-vector c'_r of template r (coefficient
+ *   encoding, Section 2.1.3) or the rounded slot-encoding coefficients of a block of templates
+ *   (Section 2.2.1 Ecd_slot, built by oracle/slots.py).
  * row_ids: values < ndb select a-part rows, ndb + r selects logical b-row r.
- * cprime: [n_rows][d2] masked bit-vectors of the selected b-rows (zero rows for padding and
- * for a-part rows).  out: [L][n_rows][K]. */
+ * msg: [n_rows][d2] message rows of the selected b-rows (zero rows for padding and for a-part
+ * rows), |m| < 2^21.  out: [L][n_rows][K]. */
 int orc_db_rows(int L, int Lq, const uint64_t *q, int ndb, int nq, int d2, int h, int eta,
                 uint64_t seed, uint64_t chunk, const int64_t *row_ids, int n_rows,
-                const int8_t *cprime, uint64_t *out) {
+                const int32_t *msg, uint64_t *out) {
     if (d2 % nq) return -1;
     const int K = d2 + nq, nqb = d2 / nq;
     int max_blk = 0;
@@ -228,7 +253,7 @@ int orc_db_rows(int L, int Lq, const uint64_t *q, int ndb, int nq, int d2, int h
 #pragma omp parallel for schedule(dynamic)
     for (int x = 0; x < n_rows; ++x) {
         if (row_ids[x] < ndb) continue;
-        const int8_t *c = cprime + (size_t)x * d2;
+        const int32_t *c = msg + (size_t)x * d2;
         int32_t *w = W + (size_t)x * K;
         for (int k = 0; k < d2; ++k) w[k] = c[k];
         /* (M_db S_q)[r][j] = sum_k' c'[t*nq + k'] * Neg(s_{q,t})[k'][j] summed over the blocks t of
