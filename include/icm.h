@@ -133,6 +133,24 @@ icm_status icm_db_encrypt(icm_ctx *ctx, const uint8_t *codes, const uint8_t *mas
                           uint64_t chunk_id, void *dev_buf, size_t bytes, void *stream, icm_db **out);
 void icm_db_destroy(icm_db *db);
 
+/* Slot-encoded database chunk (Section 2.2.1 Ecd_slot, Section 2.3: the CCMM takes a slot-encoded
+ * database matrix and its results carry the same encoding).  Templates are placed one per slot,
+ * in the slot's real part: block t of the chunk (N_db b-rows) holds templates t N_db/2 ..
+ * t N_db/2 + N_db/2 - 1 (missing ones are empty slots), so a chunk of n_db templates has
+ * ceil(n_db / (N_db/2)) full blocks.  Entry column k of block t is the rounded polynomial
+ * round(2^log2_scale P) (round half to even) with P(zeta^(5^j)) = c'_{t N_db/2 + j}[k], computed by
+ * fp64 FFT on the device; the rows are then encrypted exactly as icm_db_encrypt does with those
+ * integers as the message matrix.  icm_match, icm_rescale and icm_fold accept the handle as any
+ * other; icm_decrypt_scores refuses its scores (use icm_normalize + icm_decrypt_slots).
+ * log2_scale 1..24, and Delta 2^log2_scale d2 < Q / 4 and h (d2 / N_q)(2^log2_scale + 1) < 2^31
+ * (ICM_EBOUND otherwise).  codes/masks: host, n_db >= 1 templates; dev_buf: icm_db_bytes_slots
+ * bytes, 16-byte aligned, alive while the handle is used.  Allocates and frees temporary device
+ * memory on `stream` (the message matrix, 4 bytes per entry). */
+icm_status icm_db_bytes_slots(const icm_ctx *ctx, size_t n_db, size_t *bytes, size_t *m_rows);
+icm_status icm_db_encrypt_slots(icm_ctx *ctx, const uint8_t *codes, const uint8_t *masks, size_t n_db,
+                                uint32_t log2_scale, uint64_t chunk_id, void *dev_buf, size_t bytes, void *stream,
+                                icm_db **out);
+
 /* ---------------------------------------------------------------- query ---- */
 
 /* Bytes of the query ciphertext modulo Q (wire format) for n_eyes eyes. */
@@ -198,6 +216,32 @@ icm_status icm_decrypt_scores(icm_ctx *ctx, const icm_scores *s, int64_t *dev_nu
  * numerators are exact while it stays below 1/2. */
 icm_status icm_decrypt_scores_max_error(icm_ctx *ctx, const icm_scores *s, int64_t *dev_num, size_t n,
                                         float *dev_max_err, void *stream);
+
+/* Normalisation by the inverse mask overlaps (Algorithm 2: ct <- ct (.) mu with
+ * mu = Ecd((1 / ||m_q AND m_db||_1)_j)) of the scores of a slot-encoded chunk after icm_rescale
+ * (modulus Q, unfolded): for result column j (eye e = j / rho, rotation r = j % rho) and block t,
+ * mu_{j,t} = round(2^log2_scale_mu Ecd(v)) with v_i = 1 / ||rot_r(m_e) AND m_{t N/2 + i}||_1 (0 for
+ * an empty overlap or a missing template), and both ciphertext parts of block t are multiplied
+ * by it in Z_q[X]/(X^N + 1) for each limb of Q (negacyclic NTTs).  The output holds one full RLWE
+ * pair per (column, block): dev_out [L_q][n_cols][n_blocks][2][N_db] u64, part 0 = a-part
+ * a_j mu_{j,t}, part 1 = b_{j,t} mu_{j,t}; its slots decode to <c'_q, c'_db> / ||m_q AND m_db||_1
+ * = 1 - 2 HD at scale Delta 2^s_db 2^log2_scale_mu (no rescaling follows).  dev_q_masks: device,
+ * the n_eyes query masks (code_bits / 8 bytes each, unrotated); dev_db_masks: device, 8-byte
+ * aligned, the chunk's n_db template masks.  icm_normalize_bytes gives the sizes of dev_out and of dev_ws (rotated
+ * masks, overlaps, mu and NTT scratch).  Errors: ICM_EINVAL (not a rescaled unfolded slot-encoded
+ * result, or another context's handle), ICM_ENOMEM (buffers too small), ICM_EBOUND
+ * (Delta 2^s_db 2^log2_scale_mu >= Q / 4), ICM_ECUDA. */
+icm_status icm_normalize_bytes(const icm_scores *rescaled, size_t *out_bytes, size_t *ws_bytes);
+icm_status icm_normalize(icm_ctx *ctx, const icm_scores *rescaled, const uint8_t *dev_q_masks,
+                         const uint8_t *dev_db_masks, uint32_t log2_scale_mu, void *dev_out, size_t bytes,
+                         void *dev_ws, size_t ws_bytes, void *stream);
+/* Decryption and decoding of normalised blocks for checking only (Section 2.2.2 Dec = a sk + b
+ * under s_{db,t}; CRT over the limbs of Q to the centred integer; division by Delta 2^s_db
+ * 2^log2_scale_mu; Dcd by fp64 FFT): dev_hd [n_cols][n_db] fp64 receives the decoded fractional
+ * Hamming distance (1 - s) / 2 of every (column, template) pair.  dev_norm: icm_normalize's output.
+ * Allocates and frees temporary device memory on `stream`. */
+icm_status icm_decrypt_slots(icm_ctx *ctx, const icm_scores *rescaled, const void *dev_norm, size_t norm_bytes,
+                             uint32_t log2_scale_mu, double *dev_hd, size_t n, void *stream);
 
 /* Rescaling by Q' (Section 2.2.2, Maintenance: RS divides a ciphertext by a modulus factor and
  * rounds): scores at modulus Q_db = Q Q' (L limbs) become scores at the query modulus Q (the

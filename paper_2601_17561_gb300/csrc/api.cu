@@ -69,7 +69,7 @@ LimbTable make_limb_table(const std::vector<uint64_t> &q) {
 
 DbLayout make_layout(uint64_t n_real, uint32_t N, uint32_t rho) {
     DbLayout L{};
-    L.N = N; L.n_real = n_real;
+    L.N = N; L.n_real = n_real; L.n_tpl = n_real;
     L.n_full = (uint32_t)(n_real / N);
     L.rem = (uint32_t)(n_real % N);
     L.tail_lo = N;
@@ -107,6 +107,7 @@ icm_ctx::~icm_ctx() {
     if (d_sdb_sgn) cudaFree(d_sdb_sgn);
     if (d_sq_pos) cudaFree(d_sq_pos);
     if (d_sq_sgn) cudaFree(d_sq_sgn);
+    if (slot_tab) icm::free_slot_tables(slot_tab);
 }
 
 extern "C" {
@@ -507,6 +508,7 @@ icm_status icm_scores_shape(const icm_scores *s, size_t *n_limbs, size_t *n_cols
 icm_status icm_decrypt_scores(icm_ctx *c, const icm_scores *s, int64_t *dev_num, size_t n, void *stream) {
     if (!c || !s || !dev_num) return fail(ICM_EINVAL, "null argument");
     if (!c->have_keys) return fail(ICM_EINVAL, "icm_keygen has not run");
+    if (s->lay.slot_log2) return fail(ICM_EINVAL, "slot-encoded scores decode with icm_decrypt_slots");
     if (n < (size_t)s->n_cols * s->lay.n_real) return fail(ICM_ENOMEM, "numerator buffer too small");
     cudaError_t e = launch_decrypt(c, to_dev(s->lay), s->dev, s->n_cols, s->rescaled != 0, dev_num,
                                    (cudaStream_t)stream);
@@ -518,6 +520,7 @@ icm_status icm_decrypt_scores_max_error(icm_ctx *c, const icm_scores *s, int64_t
                                         void *stream) {
     if (!c || !s || !dev_num || !dev_max_err) return fail(ICM_EINVAL, "null argument");
     if (!c->have_keys) return fail(ICM_EINVAL, "icm_keygen has not run");
+    if (s->lay.slot_log2) return fail(ICM_EINVAL, "slot-encoded scores decode with icm_decrypt_slots");
     if (n < (size_t)s->n_cols * s->lay.n_real) return fail(ICM_ENOMEM, "numerator buffer too small");
     cudaError_t e = cudaMemsetAsync(dev_max_err, 0, sizeof(float), (cudaStream_t)stream);
     if (e == cudaSuccess)

@@ -37,16 +37,19 @@ struct DbMsgArgs {
     LayoutDev lay;
     uint32_t K, d2, Nq, nqblk, h, code_bits, L, Lq;
     const uint8_t *codes, *masks;      // [n_real][code_bits/8]
+    const int32_t *wmsg;               // message rows [n_real][d2] (slot encoding), or null: c' of codes
     const int32_t *sq_pos; const int8_t *sq_sgn;   // [nqblk][h]
     uint64_t qp[ICM_MAX_LIMBS], qps[ICM_MAX_LIMBS], q[ICM_MAX_LIMBS];
     uint64_t *db;                      // [L][M][K]
 };
 
-// Pass 1: the message residues Q' * W[r][k] of every stored b-row, for every limb.
+// Pass 1: the message residues Q' * W[r][k] of every stored b-row, for every limb.  The message
+// row is the masked bit-vector c' of template r (coefficient encoding) or, for a slot-encoded
+// chunk, the given row of rounded slot-encoding coefficients.
 __global__ void __launch_bounds__(512) k_db_messages(DbMsgArgs a) {
     extern __shared__ unsigned char smem[];
-    int8_t *cp = reinterpret_cast<int8_t *>(smem);                          // [d2]
-    int32_t *spos = reinterpret_cast<int32_t *>(smem + ((a.d2 + 15) & ~15u)); // [nqblk*h]
+    int32_t *cp = reinterpret_cast<int32_t *>(smem);                        // [d2]
+    int32_t *spos = cp + ((a.d2 + 3) & ~3u);                                // [nqblk*h]
     int8_t *ssgn = reinterpret_cast<int8_t *>(spos + a.nqblk * a.h);
 
     const uint64_t bidx = blockIdx.x;
@@ -58,11 +61,13 @@ __global__ void __launch_bounds__(512) k_db_messages(DbMsgArgs a) {
     const uint32_t tb = a.code_bits / 8;
     for (uint32_t k = threadIdx.x; k < a.d2; k += blockDim.x) {
         int v = 0;
-        if (real && k < a.code_bits) {
+        if (real && a.wmsg) {
+            v = a.wmsg[r * a.d2 + k];
+        } else if (real && k < a.code_bits) {
             const int c = template_bit(a.codes + r * tb, k), m = template_bit(a.masks + r * tb, k);
             v = m - 2 * (c & m);
         }
-        cp[k] = (int8_t)v;
+        cp[k] = v;
     }
     for (uint32_t x = threadIdx.x; x < a.nqblk * a.h; x += blockDim.x) { spos[x] = a.sq_pos[x]; ssgn[x] = a.sq_sgn[x]; }
     __syncthreads();
@@ -77,7 +82,7 @@ __global__ void __launch_bounds__(512) k_db_messages(DbMsgArgs a) {
                 // with s_{q,t}[p] != 0 contribute, with sign -1 when j + p wraps past Nq.
                 const uint32_t j = k - a.d2;
                 for (uint32_t tt = 0; tt < a.nqblk; ++tt) {
-                    const int8_t *crow = cp + tt * a.Nq;
+                    const int32_t *crow = cp + tt * a.Nq;
                     for (uint32_t c = 0; c < a.h; ++c) {
                         const uint32_t p = (uint32_t)spos[tt * a.h + c];
                         const int s = ssgn[tt * a.h + c];
@@ -219,18 +224,18 @@ __global__ void __launch_bounds__(1024) k_query_encrypt(QEncArgs a) {
 namespace icm {
 
 cudaError_t launch_db_messages(const icm_ctx *c, const LayoutDev &lay, const uint8_t *d_codes,
-                               const uint8_t *d_masks, uint64_t *d_db, cudaStream_t st) {
+                               const uint8_t *d_masks, uint64_t *d_db, cudaStream_t st, const int32_t *d_wmsg) {
     DbMsgArgs a{};
     a.lay = lay;
     a.K = c->K; a.d2 = c->p.d2; a.Nq = c->N_q; a.nqblk = c->n_qblk; a.h = c->p.hamming_weight;
     a.code_bits = c->p.code_bits; a.L = c->p.n_limbs; a.Lq = c->p.n_limbs_q;
-    a.codes = d_codes; a.masks = d_masks;
+    a.codes = d_codes; a.masks = d_masks; a.wmsg = d_wmsg;
     a.sq_pos = c->d_sq_pos; a.sq_sgn = c->d_sq_sgn;
     for (uint32_t l = 0; l < a.L; ++l) { a.qp[l] = c->qp_mod[l]; a.qps[l] = c->qp_mods[l]; a.q[l] = c->q[l]; }
     a.db = d_db;
     const uint64_t nb = lay.M - lay.N;
     if (nb == 0) return cudaSuccess;
-    const size_t smem = ((a.d2 + 15) & ~15u) + (size_t)a.nqblk * a.h * 5;
+    const size_t smem = (size_t)((a.d2 + 3) & ~3u) * 4 + (size_t)a.nqblk * a.h * 5;
     cudaError_t e = cudaFuncSetAttribute(k_db_messages, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_db_messages<<<(unsigned)nb, 512, smem, st>>>(a);

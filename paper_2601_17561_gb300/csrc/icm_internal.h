@@ -42,6 +42,8 @@ struct RescaleConsts {
 
 }  // namespace icm
 
+namespace icm { struct SlotTables; void free_slot_tables(SlotTables *t); }
+
 struct icm_ctx {
     icm_params p;
     uint32_t N_db, N_q, K, n_qblk;      // ring degrees, K = d2 + N_q, n_qblk = d2 / N_q
@@ -63,6 +65,7 @@ struct icm_ctx {
     uint32_t max_db_blocks = 0;
     int32_t *d_sdb_pos = nullptr;  int8_t *d_sdb_sgn = nullptr;   // [max_db_blocks][h]
     int32_t *d_sq_pos = nullptr;   int8_t *d_sq_sgn = nullptr;    // [n_qblk][h]
+    icm::SlotTables *slot_tab = nullptr;   // slot-encoding and NTT tables (built on first use)
     ~icm_ctx();
 };
 
@@ -75,6 +78,8 @@ struct DbLayout {
     uint32_t rem;          // real rows of the partial block (0 if none)
     uint32_t tail_lo;      // first tail coefficient of the partial block
     uint64_t M;            // stored rows
+    uint64_t n_tpl = 0;    // templates (a slot-encoded chunk holds N/2 per block)
+    uint32_t slot_log2 = 0;  // log2 of the database slot-encoding scale; 0: coefficient encoding
     uint32_t n_blocks() const { return n_full + (rem ? 1u : 0u); }
 };
 namespace icm { DbLayout make_layout(uint64_t n_real, uint32_t N, uint32_t rho); }
@@ -116,7 +121,8 @@ inline LayoutDev to_dev(const DbLayout &l) { return {l.N, l.n_full, l.rem, l.tai
 
 // ---- launchers (return cudaGetLastError of the launch)
 cudaError_t launch_db_messages(const icm_ctx *c, const LayoutDev &lay, const uint8_t *d_codes,
-                               const uint8_t *d_masks, uint64_t *d_db, cudaStream_t st);
+                               const uint8_t *d_masks, uint64_t *d_db, cudaStream_t st,
+                               const int32_t *d_wmsg = nullptr);
 cudaError_t launch_db_apart_and_b(const icm_ctx *c, const LayoutDev &lay, uint64_t chunk_id, uint64_t *d_db,
                                   cudaStream_t st);
 cudaError_t launch_query_encrypt(const icm_ctx *c, const uint8_t *d_codes, const uint8_t *d_masks,

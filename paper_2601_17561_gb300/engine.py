@@ -109,6 +109,17 @@ class Engine:
         h = C.icm_db_encrypt(self.ctx, codes, masks, n, chunk_id, buf, nbytes, stream)
         return Db(h, buf, n, m_rows, chunk_id)
 
+    def encrypt_db_slots(self, codes: np.ndarray, masks: np.ndarray, log2_scale: int = 16, chunk_id: int = 0,
+                         stream=None) -> Db:
+        """Slot-encoded database chunk (one template per slot, N_db/2 per block)."""
+        codes = np.ascontiguousarray(codes, np.uint8)
+        masks = np.ascontiguousarray(masks, np.uint8)
+        n = codes.shape[0]
+        nbytes, m_rows = C.icm_db_bytes_slots(self.ctx, n)
+        buf = _u8(nbytes, self.device)
+        h = C.icm_db_encrypt_slots(self.ctx, codes, masks, n, log2_scale, chunk_id, buf, nbytes, stream)
+        return Db(h, buf, n, m_rows, chunk_id)
+
     def encrypt_query(self, codes: np.ndarray, masks: np.ndarray, eye_ids, stream=None) -> torch.Tensor:
         codes = np.ascontiguousarray(codes, np.uint8)
         masks = np.ascontiguousarray(masks, np.uint8)
@@ -156,6 +167,23 @@ class Engine:
         buf = out if out is not None else _u8(nbytes, self.device)
         h = C.icm_rescale(self.ctx, s.handle, buf, nbytes, stream)
         return Scores(h, buf, C.icm_scores_shape(h), s.n_eyes, s.folded, s.db)
+
+    def normalize(self, s: Scores, q_masks: torch.Tensor, db_masks: torch.Tensor, log2_scale_mu: int = 36,
+                  stream=None, out: torch.Tensor = None, ws: torch.Tensor = None) -> torch.Tensor:
+        """ct (.) mu of every block of rescaled slot-encoded scores; q_masks / db_masks: device
+        uint8 packed masks.  Returns the [L_q][n_cols][n_blocks][2][N_db] residues (bytes)."""
+        ob, wb = C.icm_normalize_bytes(s.handle)
+        out = out if out is not None else _u8(ob, self.device)
+        ws = ws if ws is not None else _u8(wb, self.device)
+        C.icm_normalize(self.ctx, s.handle, q_masks, db_masks, log2_scale_mu, out, ob, ws, wb, stream)
+        return out
+
+    def decrypt_slots(self, s: Scores, norm: torch.Tensor, log2_scale_mu: int = 36, stream=None) -> torch.Tensor:
+        """Decoded fractional Hamming distances [n_cols][n_db] (device fp64) of normalised blocks."""
+        n = s.shape[1] * s.db.n_real
+        out = torch.empty(max(n, 1), dtype=torch.float64, device=self.device)
+        C.icm_decrypt_slots(self.ctx, s.handle, norm, norm.numel(), log2_scale_mu, out, n, stream)
+        return out[:n].view(s.shape[1], s.db.n_real)
 
     # -------------------------------------------------------------------- batching form
     def match_batch(self, dbs, q: Query, stream=None, outs=None, ws: torch.Tensor = None):

@@ -57,6 +57,11 @@ _SIGS = {
     "icm_keygen": (_i32, [_vp]),
     "icm_db_bytes": (_i32, [_vp, _sz, ctypes.POINTER(_sz), ctypes.POINTER(_sz)]),
     "icm_db_encrypt": (_i32, [_vp, _vp, _vp, _sz, _u64, _vp, _sz, _vp, ctypes.POINTER(_vp)]),
+    "icm_db_bytes_slots": (_i32, [_vp, _sz, ctypes.POINTER(_sz), ctypes.POINTER(_sz)]),
+    "icm_db_encrypt_slots": (_i32, [_vp, _vp, _vp, _sz, _u32, _u64, _vp, _sz, _vp, ctypes.POINTER(_vp)]),
+    "icm_normalize_bytes": (_i32, [_vp, ctypes.POINTER(_sz), ctypes.POINTER(_sz)]),
+    "icm_normalize": (_i32, [_vp, _vp, _vp, _vp, _u32, _vp, _sz, _vp, _sz, _vp]),
+    "icm_decrypt_slots": (_i32, [_vp, _vp, _vp, _sz, _u32, _vp, _sz, _vp]),
     "icm_db_destroy": (None, [_vp]),
     "icm_query_ct_bytes": (_i32, [_vp, _sz, ctypes.POINTER(_sz)]),
     "icm_query_encrypt": (_i32, [_vp, _vp, _vp, _vp, _sz, _vp, _sz, _vp]),
@@ -192,6 +197,36 @@ def icm_db_encrypt(ctx, codes, masks, n_db, chunk_id, dev_buf, nbytes, stream=No
     _check(lib().icm_db_encrypt(ctx, _ptr(codes), _ptr(masks), n_db, chunk_id, _ptr(dev_buf), nbytes,
                                 _stream(stream), ctypes.byref(h)), "icm_db_encrypt")
     return h
+
+
+def icm_db_bytes_slots(ctx, n_db: int):
+    b, m = ctypes.c_size_t(), ctypes.c_size_t()
+    _check(lib().icm_db_bytes_slots(ctx, n_db, ctypes.byref(b), ctypes.byref(m)), "icm_db_bytes_slots")
+    return b.value, m.value
+
+
+def icm_db_encrypt_slots(ctx, codes, masks, n_db, log2_scale, chunk_id, dev_buf, nbytes, stream=None):
+    h = ctypes.c_void_p()
+    _check(lib().icm_db_encrypt_slots(ctx, _ptr(codes), _ptr(masks), n_db, log2_scale, chunk_id, _ptr(dev_buf),
+                                      nbytes, _stream(stream), ctypes.byref(h)), "icm_db_encrypt_slots")
+    return h
+
+
+def icm_normalize_bytes(scores):
+    a, b = ctypes.c_size_t(), ctypes.c_size_t()
+    _check(lib().icm_normalize_bytes(scores, ctypes.byref(a), ctypes.byref(b)), "icm_normalize_bytes")
+    return a.value, b.value
+
+
+def icm_normalize(ctx, scores, dev_q_masks, dev_db_masks, log2_scale_mu, dev_out, nbytes, dev_ws, ws_bytes,
+                  stream=None):
+    _check(lib().icm_normalize(ctx, scores, _ptr(dev_q_masks), _ptr(dev_db_masks), log2_scale_mu, _ptr(dev_out),
+                               nbytes, _ptr(dev_ws), ws_bytes, _stream(stream)), "icm_normalize")
+
+
+def icm_decrypt_slots(ctx, scores, dev_norm, norm_bytes, log2_scale_mu, dev_hd, n, stream=None):
+    _check(lib().icm_decrypt_slots(ctx, scores, _ptr(dev_norm), norm_bytes, log2_scale_mu, _ptr(dev_hd), n,
+                                   _stream(stream)), "icm_decrypt_slots")
 
 
 def icm_db_destroy(h):

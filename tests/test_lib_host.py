@@ -77,6 +77,23 @@ def test_crt_moduli_cover_the_product_range(lib, cfg):
         assert len(mods) == 19
 
 
+@pytest.mark.parametrize("cfg", [O.TINY, O.PAPER])
+def test_slot_database_size(lib, cfg):
+    """A slot-encoded chunk holds N_db/2 templates per block (one per slot), all blocks full:
+    M = N_db + ceil(n_db / (N_db/2)) N_db rows of L x K words."""
+    ctx = C.icm_ctx_create(_params(**cfg))
+    try:
+        N = 1 << cfg["log_n_db"]
+        K = (1 << 14) + (1 << cfg["log_n_q"])
+        for n_db in (1, N // 2, N // 2 + 1, 3 * N + 5):
+            nbytes, m = C.icm_db_bytes_slots(ctx, n_db)
+            blocks = -(-n_db // (N // 2))
+            assert m == N + blocks * N
+            assert nbytes == cfg["n_limbs"] * m * K * 8
+    finally:
+        C.icm_ctx_destroy(ctx)
+
+
 def test_bounds_rejected(lib):
     # Delta too large: the message wraps modulo Q_db
     with pytest.raises(C.IcmError) as e:
