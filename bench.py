@@ -305,6 +305,119 @@ def run_serving(args, dev):
     return 0
 
 
+def _exact_hd(q_codes, q_masks, db_codes, db_masks, rho, dev):
+    """Cleartext fractional Hamming distances of every (eye x rotation, template) pair, from the
+    packed bits with exact fp64 matrix products on the device (a check, not the measured path):
+    HD = (||m AND m'|| - <c', c''>) / (2 ||m AND m'||) with c' = m - 2 (c AND m)."""
+    import torch
+
+    def bits(x):
+        t = torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+        b = (t.unsqueeze(-1) >> torch.arange(8, device=dev, dtype=torch.uint8)) & 1
+        return b.reshape(t.shape[0], -1)[:, :12800]
+
+    qc, qm = bits(q_codes).view(-1, 16, 200, 4), bits(q_masks).view(-1, 16, 200, 4)
+    cols_c, cols_m = [], []
+    for e in range(qc.shape[0]):
+        for r in range(rho):
+            sft = r - (rho - 1) // 2
+            cols_c.append(torch.roll(qc[e], shifts=-sft, dims=1).reshape(-1))
+            cols_m.append(torch.roll(qm[e], shifts=-sft, dims=1).reshape(-1))
+    qc, qm = torch.stack(cols_c).double(), torch.stack(cols_m).double()
+    dc, dm = bits(db_codes).double(), bits(db_masks).double()
+    qcp = qm - 2 * qc * qm
+    dcp = dm - 2 * dc * dm
+    den = qm @ dm.T
+    inner = qcp @ dcp.T
+    hd = torch.where(den > 0, (den - inner) / (2 * den.clamp(min=1)), torch.ones_like(den))
+    return hd
+
+
+def run_slots(args, dev):
+    """Slot-encoded database and normalisation (Section 2.2.1 Ecd_slot, Section 2.3, Algorithm 2's
+    ct (.) mu) on the paper's query side: 32 eyes x 31 rotations against 2^15 templates in 4
+    blocks of N_db/2 = 8,192 (one template per slot), N_db = 2^14, N_q = 2^13, 8 primes < 2^60
+    (L_q = 2), Delta 2^60, database slot scale 2^16, mu scale 2^36.  One step: query preparation,
+    CCMM (fp16 CRT form, tcgen05 kernel), rescaling by Q', normalisation; CUDA events on the
+    launching stream around each part.  The decoded distances of all pairs are compared with the
+    exact cleartext distances."""
+    import numpy as np
+    import torch
+    from paper_2601_17561_gb300 import engine as E
+    from paper_2601_17561_gb300 import icm as C
+    from paper_2601_17561_gb300 import synth
+    n_db, n_eyes, s_db, s_mu = 1 << 15, 32, 16, 36
+    W = synth.make_workload(n_eyes=n_eyes, n_db=n_db, seed=6, planted_frac=0.05)
+    eng = E.Engine(**E.PAPER).keygen()
+    t0 = time.perf_counter()
+    db = eng.encrypt_db_slots(W.db_codes, W.db_masks, log2_scale=s_db)
+    torch.cuda.synchronize()
+    enc_s = time.perf_counter() - t0
+    ct = eng.encrypt_query(W.q_codes, W.q_masks, W.eye_ids)
+    qm = torch.from_numpy(np.ascontiguousarray(W.q_masks)).to(dev)
+    dm = torch.from_numpy(np.ascontiguousarray(W.db_masks)).to(dev)
+    st = torch.cuda.Stream(device=dev)
+    q = eng.prepare(ct, n_eyes, "f16_crt", stream=st)
+    mws = eng.match_workspace(db, n_eyes, "f16_crt")
+    s = eng.match(db, q, stream=st, ws=mws)
+    r = eng.rescale(s, stream=st)
+    ob, wb = C.icm_normalize_bytes(r.handle)
+    out, ws = E._u8(ob, dev), E._u8(wb, dev)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    with torch.cuda.stream(st):
+        for _ in range(max(1, args.warmup)):
+            eng.prepare(ct, n_eyes, "f16_crt", stream=st, out=q.buf)
+            eng.match(db, q, stream=st, out=s.buf, ws=mws)
+            eng.rescale(s, stream=st, out=r.buf)
+            eng.normalize(r, qm, dm, s_mu, stream=st, out=out, ws=ws)
+        st.synchronize()
+        for e in ev:
+            e[0].record(st)
+            eng.prepare(ct, n_eyes, "f16_crt", stream=st, out=q.buf)
+            eng.match(db, q, stream=st, out=s.buf, ws=mws)
+            e[1].record(st)
+            eng.rescale(s, stream=st, out=r.buf)
+            e[2].record(st)
+            eng.normalize(r, qm, dm, s_mu, stream=st, out=out, ws=ws)
+            e[3].record(st)
+        st.synchronize()
+    ccmm = statistics.median(e[0].elapsed_time(e[1]) for e in ev)
+    resc = statistics.median(e[1].elapsed_time(e[2]) for e in ev)
+    norm = statistics.median(e[2].elapsed_time(e[3]) for e in ev)
+    step = statistics.median(e[0].elapsed_time(e[3]) for e in ev)
+    C.icm_device_status(True)
+    hd = eng.decrypt_slots(r, out, s_mu)
+    ref = _exact_hd(W.q_codes, W.q_masks, W.db_codes, W.db_masks, 31, dev)
+    err = float((hd - ref).abs().max())
+    torch.cuda.synchronize()
+    L_q, d3, N = eng.Lq, n_eyes * 31, 1 << 14
+    nb = n_db // (N // 2)
+    M = N + nb * N
+    # normalisation bytes: rescaled scores read (a-parts and b-rows), normalised pairs written
+    nbytes = L_q * d3 * M * 8 + L_q * d3 * nb * 2 * N * 8
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    line = {"metric": "slot-encoded database + normalisation: iris comparisons/s and decoded-HD error",
+            "value": n_eyes * 31 * n_db / (step / 1e3), "unit": "comparisons/s (rotations x templates)",
+            "higher_is_better": True, "n_gpus": 1, "steps": args.steps, "warmup": max(1, args.warmup),
+            "ms_per_step": step, "data": "synthetic", "dtype": "f16 CCMM, u64 NTT, f64 FFT",
+            "config": {"workload": "32 eyes x 31 rotations vs 2^15 templates, slot-encoded (4 blocks of 8,192), "
+                                   "N_db = 2^14, N_q = 2^13, 8 primes < 2^60 (L_q = 2), Delta 2^60, "
+                                   f"slot scale 2^{s_db}, mu scale 2^{s_mu}", "form": "f16_crt",
+                       "database_gb": round(db.buf.numel() / 1e9, 1)},
+            "parts_ms": {"prepare_and_ccmm": ccmm, "rescale": resc, "normalize": norm},
+            "normalize_roofline": {"bound": "hbm", "bytes": nbytes, "achieved": nbytes / (norm / 1e3) / 1e9,
+                                   "peak": hbm, "unit": "GB/s", "frac": nbytes / (norm / 1e3) / 1e9 / hbm,
+                                   "peak_source": "of measured: MEASURED_PEAKS.json hbm_gbs",
+                                   "note": "rescaled scores read once, normalised pairs written once; the "
+                                           "NTTs run in shared memory"},
+            "database_encode_s": enc_s,
+            "decode": {"hd_error_max": err, "hd_tolerance": 2.0 ** -10, "pairs": n_eyes * 31 * n_db,
+                       "reference": "exact cleartext distances (fp64 integer matrix products on the device)"}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_p2(args, dev):
     """The paper's own modulus family on its per-GPU CCMM unit (Section 6.2.2; Table 2 times it at
     259 ms on an RTX-5090): Q = prod p^2 over the 24 primes 127 <= p <= 253 (2^360.8), one database
@@ -376,9 +489,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fold-trials", type=int, default=1 << 33,
                     help="trials of the folding-polynomial check reported beside the step (0: skip)")
-    ap.add_argument("--workload", default="paper", choices=["paper", "batching", "serving", "p2"],
+    ap.add_argument("--workload", default="paper", choices=["paper", "batching", "serving", "p2", "slots"],
                     help="paper: the headline CCMM step; batching / serving: the query-batching and "
-                         "request-loop forms; p2: the paper's p^2 modulus family on one CCMM slice "
+                         "request-loop forms; p2: the paper's p^2 modulus family on one CCMM slice; "
+                         "slots: the slot-encoded database and the normalisation "
                          "(one JSON line each, not the headline)")
     ap.add_argument("--rates", default="16,32,64,128,256,512", help="serving: Poisson arrival rates (eyes/s)")
     ap.add_argument("--seconds", type=float, default=20.0, help="serving: longest submission time per rate")
@@ -406,6 +520,8 @@ def main():
         return run_serving(args, dev)
     if args.workload == "p2":
         return run_p2(args, dev)
+    if args.workload == "slots":
+        return run_slots(args, dev)
     from paper_2601_17561_gb300 import engine as E
     from paper_2601_17561_gb300 import icm as C
     from paper_2601_17561_gb300 import shard

@@ -7,8 +7,10 @@ same ring and primes: about 3 GB on the device, sized for profiler captures), sl
 4,096 codes with the paper's query side -- N_q = 2^13, d = 2^14, K = 24,576, primes < 2^60, so
 19 CRT moduli -- but N_db = 2^12 and 2 primes: M = 8,192 rows, 3.2 GB, the paper's tile shape
 and wave order at a profiler-sized scale), paper (32 eyes x 114,688 codes, N_db = 2^14,
-N_q = 2^13, 8 primes < 2^60).  Each pass prepares the query, runs the CCMM and the fold (and,
-with --rescale, the rescaling by Q').
+N_q = 2^13, 8 primes < 2^60), slots (a slot-encoded database of 1,024 templates in one block of
+N_db = 2^11, the paper's query side for 32 eyes, 4 primes < 2^60: 3.2 GB).  Each pass prepares the
+query, runs the CCMM and the fold (and, with --rescale, the rescaling by Q'); for `slots` a pass
+is the query preparation, the CCMM, the rescaling and the normalisation by the mask overlaps.
 
     python -m paper_2601_17561_gb300.run --fold-trials 268435456
 
@@ -34,6 +36,8 @@ WORKLOADS = {
     "slice": (dict(log_n_db=12, log_n_q=13, n_limbs=2, n_limbs_q=1, prime_bits=60, log2_delta=40, seed=4),
               dict(n_eyes=32, n_db=4096, seed=4, planted_frac=0.05)),
     "paper": (E.PAPER, dict(n_eyes=32, n_db=7 * (1 << 14), seed=2, planted_frac=0.05)),
+    "slots": (dict(log_n_db=11, log_n_q=13, n_limbs=4, n_limbs_q=2, prime_bits=60, log2_delta=60, seed=9),
+              dict(n_eyes=32, n_db=1024, seed=9, planted_frac=0.05)),
 }
 
 
@@ -63,8 +67,20 @@ def main(argv=None):
     eng = E.Engine(**params).keygen()
     if a.variant is not None:
         C.icm_ctx_set_variant(eng.ctx, a.variant)
-    db = eng.encrypt_db(W.db_codes, W.db_masks)
     ct = eng.encrypt_query(W.q_codes, W.q_masks, W.eye_ids)
+    if a.workload == "slots":
+        db = eng.encrypt_db_slots(W.db_codes, W.db_masks, log2_scale=16)
+        qm = torch.from_numpy(W.q_masks.copy()).to(eng.device)
+        dm = torch.from_numpy(W.db_masks.copy()).to(eng.device)
+        torch.cuda.synchronize()
+        for i in range(a.passes):
+            t0 = time.perf_counter()
+            r = eng.rescale(eng.match(db, eng.prepare(ct, wl["n_eyes"], a.form)))
+            eng.normalize(r, qm, dm, 36)
+            torch.cuda.synchronize()
+            print(f"pass {i}: {(time.perf_counter() - t0) * 1e3:.1f} ms (slots, {a.form})", flush=True)
+        return 0
+    db = eng.encrypt_db(W.db_codes, W.db_masks)
     torch.cuda.synchronize()
     for i in range(a.passes):
         t0 = time.perf_counter()
