@@ -309,6 +309,7 @@ def _exact_hd(q_codes, q_masks, db_codes, db_masks, rho, dev):
     """Cleartext fractional Hamming distances of every (eye x rotation, template) pair, from the
     packed bits with exact fp64 matrix products on the device (a check, not the measured path):
     HD = (||m AND m'|| - <c', c''>) / (2 ||m AND m'||) with c' = m - 2 (c AND m)."""
+    import numpy as np
     import torch
 
     def bits(x):
