@@ -746,12 +746,11 @@ def main():
            "d2h_bytes_per_step": fo_bytes, "ms_per_step": te}
     del wsbuf
 
-    # kernels per step: query basis extension (+ residue planes), the product (CRT forms: a phase-1
-    # launch and a combine per column round -- 512 columns for mma.sync, 1,024 for tcgen05), fold
-    tc_run = args.form == "f16_crt" and tune is not None and tune.get("chosen") in (1, 2, 3)
-    n_rounds = (N_EYES * 31 + (1023 if tc_run else 511)) // (1024 if tc_run else 512)
+    # kernels per step: query basis extension (+ residue planes), the product's launches as the
+    # library reports them (CRT forms: a product and a recombination launch per column round and
+    # limb group), fold
     launches_per_step = 1 + (1 if args.form != "u64" else 0) + \
-        (2 * n_rounds if args.form in ("i8_crt", "f16_crt") else 1) + 1
+        C.icm_match_launches(eng.ctx, db.handle, N_EYES, C.FORMS[args.form]) + 1
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": max(args.warmup, 1), "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.form], "data": "synthetic",

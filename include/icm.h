@@ -184,6 +184,12 @@ icm_status icm_scores_bytes(const icm_ctx *ctx, const icm_db *db, size_t n_eyes,
  * fp16 CRT form keeps one byte per output residue and modulus). */
 icm_status icm_match_workspace_bytes(const icm_ctx *ctx, const icm_db *db, size_t n_eyes, icm_form form, size_t *bytes);
 
+/* Kernel launches that icm_match enqueues for n_eyes eyes in `form` on this chunk with the
+ * context's current variant: 1 for the u64 and digit forms; for the CRT forms a product launch
+ * and a recombination launch per column round (1,024 columns on the tcgen05 kernel, 512 on
+ * mma.sync) and per group of limbs (the groups keep the residue scratch within 6 GiB). */
+icm_status icm_match_launches(const icm_ctx *ctx, const icm_db *db, size_t n_eyes, icm_form form, size_t *n);
+
 /* CCMM (Section 2.3): C = [A1 A2; B1 B2] * [B_q; A_q] per limb, i.e. the four plaintext modular
  * products fused into one [M x K] x [K x d3] product per RNS limb, in the query's form.  Output
  * bit-identical across forms.  dev_out: icm_scores_bytes(folded = 0); dev_ws:

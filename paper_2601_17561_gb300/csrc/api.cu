@@ -438,6 +438,20 @@ icm_status icm_match_workspace_bytes(const icm_ctx *c, const icm_db *db, size_t 
     return ICM_OK;
 }
 
+icm_status icm_match_launches(const icm_ctx *c, const icm_db *db, size_t n_eyes, icm_form form, size_t *n) {
+    if (!c || !db || !n) return fail(ICM_EINVAL, "null argument");
+    const uint64_t N = (uint64_t)n_eyes * c->p.rho, M = db->lay.M;
+    *n = 0;
+    if (N == 0 || M == 0) return ICM_OK;
+    if (form == ICM_FORM_U64 || form == ICM_FORM_I8_DIGITS) { *n = 1; return ICM_OK; }
+    if (form != ICM_FORM_I8_CRT && form != ICM_FORM_F16_CRT) return fail(ICM_EINVAL, "not a match form");
+    const uint32_t L = c->p.n_limbs, G = crt_limb_group(L, c->i8_crt.n_mod, N, M);
+    const bool tc = form == ICM_FORM_F16_CRT && crt_tc_variant(c->crt_bn) && crt_tc_supported(c->K);
+    const uint64_t cols = tc ? 1024 : 512;
+    *n = (size_t)((L + G - 1) / G) * ((N + cols - 1) / cols) * 2;
+    return ICM_OK;
+}
+
 icm_status icm_match(icm_ctx *c, const icm_db *db, const icm_query *q, void *dev_out, size_t bytes, void *dev_ws,
                      size_t ws_bytes, void *stream, icm_scores **out) {
     if (!c || !db || !q || !dev_out || !out) return fail(ICM_EINVAL, "null argument");

@@ -57,6 +57,7 @@ _SIGS = {
     "icm_keygen": (_i32, [_vp]),
     "icm_db_bytes": (_i32, [_vp, _sz, ctypes.POINTER(_sz), ctypes.POINTER(_sz)]),
     "icm_db_encrypt": (_i32, [_vp, _vp, _vp, _sz, _u64, _vp, _sz, _vp, ctypes.POINTER(_vp)]),
+    "icm_match_launches": (_i32, [_vp, _vp, _sz, ctypes.c_int, ctypes.POINTER(_sz)]),
     "icm_db_bytes_slots": (_i32, [_vp, _sz, ctypes.POINTER(_sz), ctypes.POINTER(_sz)]),
     "icm_db_encrypt_slots": (_i32, [_vp, _vp, _vp, _sz, _u32, _u64, _vp, _sz, _vp, ctypes.POINTER(_vp)]),
     "icm_normalize_bytes": (_i32, [_vp, ctypes.POINTER(_sz), ctypes.POINTER(_sz)]),
@@ -197,6 +198,12 @@ def icm_db_encrypt(ctx, codes, masks, n_db, chunk_id, dev_buf, nbytes, stream=No
     _check(lib().icm_db_encrypt(ctx, _ptr(codes), _ptr(masks), n_db, chunk_id, _ptr(dev_buf), nbytes,
                                 _stream(stream), ctypes.byref(h)), "icm_db_encrypt")
     return h
+
+
+def icm_match_launches(ctx, db, n_eyes: int, form) -> int:
+    n = _sz()
+    _check(lib().icm_match_launches(ctx, db, n_eyes, form, ctypes.byref(n)), "icm_match_launches")
+    return n.value
 
 
 def icm_db_bytes_slots(ctx, n_db: int):

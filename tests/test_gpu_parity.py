@@ -419,3 +419,18 @@ def test_rescale_rejects_misuse(gpu_run):
     with pytest.raises(C.IcmError) as e:
         C.icm_rescale(eng.ctx, gpu_run["s"].handle, small, 8)
     assert e.value.status == C.ICM_ENOMEM
+
+
+def test_match_launch_count(tiny, gpu_run):
+    """icm_match_launches: one launch for the u64 and digit forms; for the CRT forms a product and
+    a recombination launch per column round (1,024 columns on tcgen05, 512 on mma.sync) and limb
+    group (the tiny residue scratch holds all three limbs in one group)."""
+    from paper_2601_17561_gb300 import icm as C
+    eng, db = gpu_run["eng"], gpu_run["db"]
+    n_eyes = tiny["W"].q_codes.shape[0]                          # 124 columns: one round
+    assert C.icm_match_launches(eng.ctx, db.handle, n_eyes, C.FORMS["u64"]) == 1
+    assert C.icm_match_launches(eng.ctx, db.handle, n_eyes, C.FORMS["i8_digits"]) == 1
+    assert C.icm_match_launches(eng.ctx, db.handle, n_eyes, C.FORMS["f16_crt"]) == 2
+    assert C.icm_match_launches(eng.ctx, db.handle, 20, C.FORMS["i8_crt"]) == 4     # 620 columns: 2 rounds of 512
+    assert C.icm_match_launches(eng.ctx, db.handle, 40, C.FORMS["f16_crt"]) == 4    # 1,240 columns: 2 of 1,024
+    assert C.icm_match_launches(eng.ctx, db.handle, 0, C.FORMS["f16_crt"]) == 0
