@@ -24,7 +24,7 @@
 //    K 16) into the tile's accumulator and one commit.  An operand slot (A residues + both tiles'
 //    B planes) has a "full" and an "empty" barrier per column tile, so each issuer waits once and
 //    commits once per slab;
-//  * epilogue (4 warps, one TMEM lane quarter each): reduces an accumulator in place
+//  * epilogue (4 warps, one per TMEM lane quarter): reduces an accumulator in place
 //    (tcgen05.ld / st) at its reduction points or writes the final residues.  The two tiles'
 //    reduction points are staggered by half an interval (tile 1 at slabs 31, 95, ..., tile 0 at
 //    63, 127, ...), so the tensor cores keep working on one tile while the other is reduced.
@@ -62,11 +62,12 @@ constexpr uint32_t TMEM_COLS = 512;               // two 256-column fp32 accumul
 constexpr int FLUSH = 64;                         // slabs (1024 columns of K) between reductions
 constexpr int STAGGER = FLUSH / 2;                // offset of the second accumulator's reductions
 constexpr int NCV = 8;                            // converter warps
-constexpr int NEP = 4;                            // epilogue warps, one TMEM lane quarter each
+constexpr int NEP = 8;                            // epilogue warps: NEP / 4 per TMEM lane quarter
+constexpr int EP_COLS = BN / (NEP / 4);           // accumulator columns of one epilogue warp
 // warps: converters, epilogue, raw database producer, query-plane producers of column tiles 0 and
 // 1, MMA issuers of column tiles 0 and 1
 constexpr int W_EPI = NCV, W_RAW = NCV + NEP, W_QRY = W_RAW + 1, W_MMA = W_QRY + 2;
-constexpr int NTHREADS = (W_MMA + 2) * 32;        // 17 warps
+constexpr int NTHREADS = (W_MMA + 2) * 32;        // 21 warps
 constexpr uint64_t ROUND = 2 * BN;                // columns of one round (one block's accumulators)
 constexpr uint64_t LAUNCH_COLS = 1024;            // columns of one launch (its rounds): the scratch width
 
@@ -421,6 +422,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_crt_tc(const __grid_constant__ 
     } else if (warp < W_EPI + NEP) {
         // ------------------------------------------------------------------ epilogue warps
         const uint32_t qtr = (uint32_t)warp & 3;                          // TMEM lane quarter
+        const uint32_t half = (uint32_t)(warp - W_EPI) >> 2;              // column part of the accumulator
         const uint32_t trow = qtr * 32 + lane;                            // accumulator row of this thread
         uint32_t ev[2] = {0, 0};                                          // accfull completions consumed
         bool alive = true;
@@ -434,31 +436,36 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_crt_tc(const __grid_constant__ 
                 if (!ok) return false;
                 ++ev[j];
                 tc_fence_after();
-                const uint32_t tbase = tmem + ((qtr * 32) << 16) + j * BN;
-                for (uint32_t c = 0; c < BN / 32; ++c) {
+                const uint32_t tbase = tmem + ((qtr * 32) << 16) + j * BN + half * EP_COLS;
+                // x - m round(x / m): the fma adds 1.5 2^23 to the exact x / m estimate and rounds
+                // once, which rounds it to an integer (|x / m| < 2^22); the result is an exact
+                // integer in (-m, m)
+                auto reduce = [&](uint32_t (&v)[32]) {
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        const float x = __uint_as_float(v[i]);
+                        const float t = __fsub_rn(fmaf(x, md.inv_m, 12582912.0f), 12582912.0f);
+                        v[i] = __float_as_uint(fmaf(-fm, t, x));
+                    }
+                };
+                for (uint32_t c = 0; c < EP_COLS / 32; ++c) {
                     uint32_t v[32];
                     tmem_ld32_nw(tbase + c * 32, v);
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    reduce(v);
                     if (!final) {
-                        // x - m round(x / m): the fma adds 1.5 2^23 to the exact x / m estimate and
-                        // rounds once, which rounds it to an integer (|x / m| < 2^22)
-#pragma unroll
-                        for (int i = 0; i < 32; ++i) {
-                            const float x = __uint_as_float(v[i]);
-                            const float t = __fsub_rn(fmaf(x, md.inv_m, 12582912.0f), 12582912.0f);
-                            v[i] = __float_as_uint(fmaf(-fm, t, x));
-                        }
                         tmem_st32(tbase + c * 32, v);
                     } else {
                         const uint64_t row = tc.m0 + trow;
                         uint8_t *Rl = p.R + ((size_t)tc.l * p.n_mod + tc.mi) * p.nch * Mall + p.tab.row0[tc.c];
+                        const uint64_t col0 = tc.col_base + j * BN + half * EP_COLS + c * 32;   // column of the launch
 #pragma unroll
                         for (int i = 0; i < 32; ++i) {
-                            const uint64_t col = tc.col_base + j * BN + c * 32 + i;      // column of the launch
+                            const uint64_t col = col0 + i;
                             if (row < tc.M && col < p.nch && p.n0 + col < p.N) {
-                                int val = __float2int_rn(__uint_as_float(v[i])) % md.m;
-                                val = val < 0 ? val + md.m : val;
-                                Rl[col * Mall + row] = (uint8_t)val;
+                                float r = __uint_as_float(v[i]);
+                                r = r < 0.0f ? r + fm : r;
+                                Rl[col * Mall + row] = (uint8_t)__float2int_rn(r);
                             }
                         }
                     }
@@ -652,15 +659,20 @@ cudaError_t launch_variant(const TcArgs &a, int sms, cudaStream_t st) {
     return cudaLaunchKernelEx(&cfg, k_crt_tc<NCG, SYNC, RS, S>, a);
 }
 
+template <int NCG, bool SYNC, int RS, int S>
+cudaError_t set_smem_attr() {
+    return cudaFuncSetAttribute(k_crt_tc<NCG, SYNC, RS, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                Ring<RS, S>::SMEM);
+}
+
 }  // namespace
 
 namespace icm {
 
 cudaError_t crt_tc_set_attributes() {
-    const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    cudaError_t e = cudaFuncSetAttribute(k_crt_tc<ICM_TC_V1>, attr, Ring<8, 4>::SMEM);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_crt_tc<ICM_TC_V2>, attr, Ring<8, 4>::SMEM);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_crt_tc<ICM_TC_V3>, attr, Ring<4, 8>::SMEM);
+    cudaError_t e = set_smem_attr<ICM_TC_V1>();
+    if (e == cudaSuccess) e = set_smem_attr<ICM_TC_V2>();
+    if (e == cudaSuccess) e = set_smem_attr<ICM_TC_V3>();
     return e;
 }
 
