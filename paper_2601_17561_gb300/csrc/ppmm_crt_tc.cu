@@ -238,6 +238,20 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32
                  : "memory");
 }
 
+// 16 columns of 32-bit TMEM words per thread (lane quarter of the warp), without the wait
+__device__ __forceinline__ void tmem_ld16_nw(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
+                 :: "r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+                    "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+                 : "memory");
+}
+
 // Residues modulo m of two balanced-digit storage words, as f16x2 bits, in integer arithmetic:
 // v = sum_t d_t (256^t mod m) + c lies in [0, 2^19) (|sum| <= 2^17, c = m ceil(2^17 / m) + h),
 // x = v - m floor(v / m) in [0, m) with the quotient from one multiply-high by ceil(2^32 / m)
@@ -440,35 +454,47 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_crt_tc(const __grid_constant__ 
                 // x - m round(x / m): the fma adds 1.5 2^23 to the exact x / m estimate and rounds
                 // once, which rounds it to an integer (|x / m| < 2^22); the result is an exact
                 // integer in (-m, m)
-                auto reduce = [&](uint32_t (&v)[32]) {
+                const uint64_t row = tc.m0 + trow;
+                uint8_t *Rl = p.R + ((size_t)tc.l * p.n_mod + tc.mi) * p.nch * Mall + p.tab.row0[tc.c];
+                auto emit = [&](uint32_t (&v)[16], uint32_t c) {
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) {
+                    for (int i = 0; i < 16; ++i) {
                         const float x = __uint_as_float(v[i]);
                         const float t = __fsub_rn(fmaf(x, md.inv_m, 12582912.0f), 12582912.0f);
                         v[i] = __float_as_uint(fmaf(-fm, t, x));
                     }
-                };
-                for (uint32_t c = 0; c < EP_COLS / 32; ++c) {
-                    uint32_t v[32];
-                    tmem_ld32_nw(tbase + c * 32, v);
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                    reduce(v);
                     if (!final) {
-                        tmem_st32(tbase + c * 32, v);
-                    } else {
-                        const uint64_t row = tc.m0 + trow;
-                        uint8_t *Rl = p.R + ((size_t)tc.l * p.n_mod + tc.mi) * p.nch * Mall + p.tab.row0[tc.c];
-                        const uint64_t col0 = tc.col_base + j * BN + half * EP_COLS + c * 32;   // column of the launch
-#pragma unroll
-                        for (int i = 0; i < 32; ++i) {
-                            const uint64_t col = col0 + i;
-                            if (row < tc.M && col < p.nch && p.n0 + col < p.N) {
-                                float r = __uint_as_float(v[i]);
-                                r = r < 0.0f ? r + fm : r;
-                                Rl[col * Mall + row] = (uint8_t)__float2int_rn(r);
-                            }
-                        }
+                        tmem_st16(tbase + c * 16, v);
+                        return;
                     }
+                    const uint64_t col0 = tc.col_base + j * BN + half * EP_COLS + c * 16;   // column of the launch
+                    uint8_t *dst = Rl + col0 * Mall + row;
+                    if (row < tc.M && col0 + 16 <= p.nch && p.n0 + col0 + 16 <= p.N) {
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) {
+                            const float r = __uint_as_float(v[i]);
+                            dst[i * Mall] = (uint8_t)__float2int_rn(r < 0.0f ? r + fm : r);
+                        }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 16; ++i)
+                            if (row < tc.M && col0 + i < p.nch && p.n0 + col0 + i < p.N) {
+                                const float r = __uint_as_float(v[i]);
+                                dst[i * Mall] = (uint8_t)__float2int_rn(r < 0.0f ? r + fm : r);
+                            }
+                    }
+                };
+                // 16 columns per load, the next load in flight while the current chunk is reduced
+                uint32_t va[16], vb[16];
+                tmem_ld16_nw(tbase, va);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                for (uint32_t c = 0; c < EP_COLS / 16; c += 2) {
+                    tmem_ld16_nw(tbase + (c + 1) * 16, vb);
+                    emit(va, c);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    if (c + 2 < EP_COLS / 16) tmem_ld16_nw(tbase + (c + 2) * 16, va);
+                    emit(vb, c + 1);
+                    if (c + 2 < EP_COLS / 16) asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                 }
                 if (!final) asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 tc_fence_before();
