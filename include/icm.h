@@ -383,9 +383,14 @@ icm_status icm_match_host_workspace_bytes(const icm_ctx *ctx, const icm_db *db, 
 /* One whole matching pass from host memory to host memory, enqueued on `stream`: copy the query
  * ciphertext (wire format, host_ct, icm_query_ct_bytes bytes) to the device, prepare it (basis
  * extension and planes of `form`), CCMM against `db` (Section 2.3), fold (Algorithm 2), and copy
- * the folded scores ([L][n_eyes * ceil(rho / fold_k)][M] u64) to host_folded.  Host buffers should
- * be page-locked for asynchronous copies; they must stay valid until the stream reaches the end
- * of this work.  dev_ws: icm_match_host_workspace_bytes bytes of caller device memory. */
+ * the folded scores ([L][n_eyes * ceil(rho / fold_k)][M] u64) to host_folded.  The eyes run in two
+ * parts (ceil(n_eyes / 2), then the rest) so that part 2's ciphertext copy overlaps part 1's
+ * product and part 1's result copy overlaps part 2's product, on a copy stream the call creates
+ * and joins back into `stream` (when `stream` completes, so has all of the call's work).  Host
+ * buffers should be page-locked for asynchronous copies; they must stay valid until the stream
+ * reaches the end of this work.  dev_ws: icm_match_host_workspace_bytes bytes of caller device
+ * memory.  Errors: ICM_EINVAL (null arguments, no eyes), ICM_ENOMEM (workspace too small), and
+ * those of icm_query_prepare, icm_match and icm_fold. */
 icm_status icm_match_host(icm_ctx *ctx, const icm_db *db, const uint64_t *host_ct, size_t n_eyes, icm_form form,
                           uint64_t *host_folded, void *dev_ws, size_t ws_bytes, void *stream);
 

@@ -572,48 +572,128 @@ icm_status icm_rescale(icm_ctx *c, const icm_scores *in, void *dev_out, size_t b
 
 static size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
-icm_status icm_match_host_workspace_bytes(const icm_ctx *c, const icm_db *db, size_t n_eyes, icm_form form,
-                                          size_t *bytes) {
-    if (!c || !db || !bytes) return fail(ICM_EINVAL, "null argument");
-    size_t ct, op, sc, fo, mw;
+// icm_match_host runs the eyes in two parts so that the copies of one part overlap the product of
+// the other: the query ciphertext of part 2 is copied in while part 1 is prepared and matched, and
+// the folded scores of part 1 are copied out while part 2 is matched.  Workspace: the ciphertext
+// of both parts, the operand, scores and match workspace of the larger part (reused in turn), and
+// the folded scores of both parts.
+struct HostParts {
+    size_t n1, n2;
+    size_t ct1, ct2, op, sc, mw, fo1, fo2;
+    size_t off_ct2, off_op, off_sc, off_mw, off_fo1, off_fo2, total;
+};
+static icm_status host_parts(const icm_ctx *c, const icm_db *db, size_t n_eyes, icm_form form, HostParts &h) {
+    h.n1 = (n_eyes + 1) / 2;
+    h.n2 = n_eyes - h.n1;
     icm_status s;
-    if ((s = icm_query_ct_bytes(c, n_eyes, &ct)) != ICM_OK) return s;
-    if ((s = icm_query_op_bytes(c, n_eyes, form, &op)) != ICM_OK) return s;
-    if ((s = icm_scores_bytes(c, db, n_eyes, 0, &sc)) != ICM_OK) return s;
-    if ((s = icm_scores_bytes(c, db, n_eyes, 1, &fo)) != ICM_OK) return s;
-    if ((s = icm_match_workspace_bytes(c, db, n_eyes, form, &mw)) != ICM_OK) return s;
-    *bytes = align256(ct) + align256(op) + align256(sc) + align256(fo) + align256(mw);
+    if ((s = icm_query_ct_bytes(c, h.n1, &h.ct1)) != ICM_OK) return s;
+    if ((s = icm_query_ct_bytes(c, h.n2, &h.ct2)) != ICM_OK) return s;
+    if ((s = icm_query_op_bytes(c, h.n1, form, &h.op)) != ICM_OK) return s;
+    if ((s = icm_scores_bytes(c, db, h.n1, 0, &h.sc)) != ICM_OK) return s;
+    if ((s = icm_match_workspace_bytes(c, db, h.n1, form, &h.mw)) != ICM_OK) return s;
+    if ((s = icm_scores_bytes(c, db, h.n1, 1, &h.fo1)) != ICM_OK) return s;
+    if ((s = icm_scores_bytes(c, db, h.n2, 1, &h.fo2)) != ICM_OK) return s;
+    h.off_ct2 = align256(h.ct1);
+    h.off_op = h.off_ct2 + align256(h.ct2);
+    h.off_sc = h.off_op + align256(h.op);
+    h.off_mw = h.off_sc + align256(h.sc);
+    h.off_fo1 = h.off_mw + align256(h.mw);
+    h.off_fo2 = h.off_fo1 + align256(h.fo1);
+    h.total = h.off_fo2 + align256(h.fo2);
     return ICM_OK;
 }
 
-icm_status icm_match_host(icm_ctx *c, const icm_db *db, const uint64_t *host_ct, size_t n_eyes, icm_form form,
-                          uint64_t *host_folded, void *dev_ws, size_t ws_bytes, void *stream) {
-    if (!c || !db || !host_ct || !host_folded || !dev_ws) return fail(ICM_EINVAL, "null argument");
-    size_t need, ct, op, sc, fo, mw;
-    icm_status s = icm_match_host_workspace_bytes(c, db, n_eyes, form, &need);
+icm_status icm_match_host_workspace_bytes(const icm_ctx *c, const icm_db *db, size_t n_eyes, icm_form form,
+                                          size_t *bytes) {
+    if (!c || !db || !bytes) return fail(ICM_EINVAL, "null argument");
+    HostParts h;
+    icm_status s = host_parts(c, db, n_eyes, form, h);
     if (s != ICM_OK) return s;
-    if (ws_bytes < need) return fail(ICM_ENOMEM, "workspace too small");
-    icm_query_ct_bytes(c, n_eyes, &ct);
-    icm_query_op_bytes(c, n_eyes, form, &op);
-    icm_scores_bytes(c, db, n_eyes, 0, &sc);
-    icm_scores_bytes(c, db, n_eyes, 1, &fo);
-    icm_match_workspace_bytes(c, db, n_eyes, form, &mw);
-    char *w = (char *)dev_ws;
-    void *d_ct = w, *d_op = w + align256(ct), *d_sc = w + align256(ct) + align256(op);
-    void *d_fo = w + align256(ct) + align256(op) + align256(sc);
-    void *d_mw = w + align256(ct) + align256(op) + align256(sc) + align256(fo);
-    cudaStream_t st = (cudaStream_t)stream;
-    CUDA_TRY(cudaMemcpyAsync(d_ct, host_ct, ct, cudaMemcpyHostToDevice, st));
+    *bytes = h.total;
+    return ICM_OK;
+}
+
+// prepare, match and fold one part of the eyes (device buffers of the part)
+static icm_status host_part(icm_ctx *c, const icm_db *db, const void *d_ct, size_t n, icm_form form, void *d_op,
+                            size_t op, void *d_sc, size_t sc, void *d_mw, size_t mw, void *d_fo, size_t fo,
+                            void *stream) {
     icm_query *q = nullptr;
     icm_scores *m = nullptr, *f = nullptr;
-    if ((s = icm_query_prepare(c, d_ct, n_eyes, form, d_op, op, stream, &q)) != ICM_OK) return s;
+    icm_status s = icm_query_prepare(c, d_ct, n, form, d_op, op, stream, &q);
+    if (s != ICM_OK) return s;
     s = icm_match(c, db, q, d_sc, sc, mw ? d_mw : nullptr, mw, stream, &m);
     if (s == ICM_OK) s = icm_fold(c, m, d_fo, fo, stream, &f);
     icm_query_destroy(q);
     icm_scores_destroy(m);
     icm_scores_destroy(f);
+    return s;
+}
+
+icm_status icm_match_host(icm_ctx *c, const icm_db *db, const uint64_t *host_ct, size_t n_eyes, icm_form form,
+                          uint64_t *host_folded, void *dev_ws, size_t ws_bytes, void *stream) {
+    if (!c || !db || !host_ct || !host_folded || !dev_ws) return fail(ICM_EINVAL, "null argument");
+    if (n_eyes == 0) return fail(ICM_EINVAL, "no eyes");
+    HostParts h;
+    icm_status s = host_parts(c, db, n_eyes, form, h);
     if (s != ICM_OK) return s;
-    CUDA_TRY(cudaMemcpyAsync(host_folded, d_fo, fo, cudaMemcpyDeviceToHost, st));
+    if (ws_bytes < h.total) return fail(ICM_ENOMEM, "workspace too small");
+    char *w = (char *)dev_ws;
+    cudaStream_t st = (cudaStream_t)stream;
+    // wire format [Lq][n rho][K]: part p holds eyes [e0, e0 + n_p) as its own wire-format buffer;
+    // folded scores [L][n G][M] (G folded columns per eye): part p's rows of every limb
+    const size_t Lq = c->p.n_limbs_q, L = c->p.n_limbs, rho = c->p.rho, K = c->K;
+    const size_t G = (rho + c->p.fold_k - 1) / c->p.fold_k, M = db->lay.M;
+    const size_t ct_row = rho * K * 8, fo_row = G * M * 8;           // bytes per eye and limb
+    auto h2d = [&](void *dst, size_t e0, size_t n, cudaStream_t s2) {
+        return cudaMemcpy2DAsync(dst, n * ct_row, reinterpret_cast<const char *>(host_ct) + e0 * ct_row,
+                                 n_eyes * ct_row, n * ct_row, Lq, cudaMemcpyHostToDevice, s2);
+    };
+    auto d2h = [&](const void *src, size_t e0, size_t n, cudaStream_t s2) {
+        return cudaMemcpy2DAsync(reinterpret_cast<char *>(host_folded) + e0 * fo_row, n_eyes * fo_row, src,
+                                 n * fo_row, n * fo_row, L, cudaMemcpyDeviceToHost, s2);
+    };
+    if (h.n2 == 0) {                                                 // a single eye: no second part
+        CUDA_TRY(h2d(w, 0, h.n1, st));
+        s = host_part(c, db, w, h.n1, form, w + h.off_op, h.op, w + h.off_sc, h.sc, w + h.off_mw, h.mw,
+                      w + h.off_fo1, h.fo1, stream);
+        if (s != ICM_OK) return s;
+        CUDA_TRY(d2h(w + h.off_fo1, 0, h.n1, st));
+        return ICM_OK;
+    }
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ev_start = nullptr, ev_h2 = nullptr, ev_f1 = nullptr, ev_d1 = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    for (cudaEvent_t *ev : {&ev_start, &ev_h2, &ev_f1, &ev_d1})
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    // the copy stream starts after the caller's earlier work on `stream` (which may still read
+    // this workspace)
+    if (e == cudaSuccess) e = cudaEventRecord(ev_start, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev_start, 0);
+    if (e == cudaSuccess) e = h2d(w, 0, h.n1, st);
+    if (e == cudaSuccess) e = h2d(w + h.off_ct2, h.n1, h.n2, cs);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_h2, cs);
+    if (e == cudaSuccess) {
+        s = host_part(c, db, w, h.n1, form, w + h.off_op, h.op, w + h.off_sc, h.sc, w + h.off_mw, h.mw,
+                      w + h.off_fo1, h.fo1, stream);
+        if (s == ICM_OK) {
+            e = cudaEventRecord(ev_f1, st);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev_f1, 0);
+            if (e == cudaSuccess) e = d2h(w + h.off_fo1, 0, h.n1, cs);
+            if (e == cudaSuccess) e = cudaEventRecord(ev_d1, cs);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev_h2, 0);
+            if (e == cudaSuccess)
+                s = host_part(c, db, w + h.off_ct2, h.n2, form, w + h.off_op, h.op, w + h.off_sc, h.sc,
+                              w + h.off_mw, h.mw, w + h.off_fo2, h.fo2, stream);
+            if (e == cudaSuccess && s == ICM_OK) e = d2h(w + h.off_fo2, h.n1, h.n2, st);
+            // the caller's stream completes only after both parts' copies
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev_d1, 0);
+        }
+    }
+    for (cudaEvent_t ev : {ev_start, ev_h2, ev_f1, ev_d1})
+        if (ev) cudaEventDestroy(ev);
+    if (cs) cudaStreamDestroy(cs);
+    if (s != ICM_OK) return s;
+    if (e != cudaSuccess) return fail(ICM_ECUDA, std::string("match_host: ") + cudaGetErrorString(e));
     return ICM_OK;
 }
 

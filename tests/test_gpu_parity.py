@@ -434,3 +434,27 @@ def test_match_launch_count(tiny, gpu_run):
     assert C.icm_match_launches(eng.ctx, db.handle, 20, C.FORMS["i8_crt"]) == 4     # 620 columns: 2 rounds of 512
     assert C.icm_match_launches(eng.ctx, db.handle, 40, C.FORMS["f16_crt"]) == 4    # 1,240 columns: 2 of 1,024
     assert C.icm_match_launches(eng.ctx, db.handle, 0, C.FORMS["f16_crt"]) == 0
+
+
+@pytest.mark.parametrize("n_eyes,form", [(4, "u64"), (3, "f16_crt"), (1, "f16_crt")])
+def test_match_host_buffers(tiny, gpu_run, n_eyes, form):
+    """icm_match_host (host ciphertext in, host folded scores out; the eyes run in two parts whose
+    copies overlap the other part's product) gives the oracle's folded residues for an even, an
+    odd and a single-eye batch."""
+    from paper_2601_17561_gb300 import icm as C
+    P, W = tiny["P"], tiny["W"]
+    eng, db = gpu_run["eng"], gpu_run["db"]
+    ct = eng.encrypt_query(W.q_codes[:n_eyes], W.q_masks[:n_eyes], W.eye_ids[:n_eyes])
+    h_ct = ct.cpu().pin_memory()
+    G = (P.rho + P.fold_k - 1) // P.fold_k
+    L, M = P.n_limbs, db.m_rows
+    h_fo = torch.zeros(L * n_eyes * G * M * 8, dtype=torch.uint8).pin_memory()
+    f = C.FORMS[form]
+    wsb = C.icm_match_host_workspace_bytes(eng.ctx, db.handle, n_eyes, f)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=eng.device)
+    st = torch.cuda.Stream()
+    C.icm_match_host(eng.ctx, db.handle, h_ct, n_eyes, f, h_fo, ws, wsb, stream=st)
+    st.synchronize()
+    got = h_fo.view(torch.int64).numpy().view(np.uint64).reshape(L, n_eyes * G, M)
+    want = O.fold(P, tiny["C"][:, : n_eyes * P.rho], tiny["ids"], n_eyes=n_eyes, n_real=W.db_codes.shape[0])
+    assert np.array_equal(got, want)
