@@ -360,7 +360,7 @@ struct FwdArgs {
     const uint64_t *src; uint64_t src_ls, src_ps;
     uint64_t *dst; uint64_t dst_ls, dst_ps;
 };
-__global__ void __launch_bounds__(512) k_ntt_fwd(FwdArgs a) {
+__global__ void __launch_bounds__(1024) k_ntt_fwd(FwdArgs a) {
     extern __shared__ uint64_t su[];
     const uint64_t total = (uint64_t)a.Lq * a.per_limb;
     for (uint64_t x = blockIdx.x; x < total; x += gridDim.x) {
@@ -388,7 +388,7 @@ struct MulArgs {
     const uint64_t *mu_ntt;         // [Lq][n_cols][n_blocks][N]
     uint64_t *out;                  // [Lq][n_cols][n_blocks][2][N]
 };
-__global__ void __launch_bounds__(512) k_ntt_mul_inv(MulArgs a) {
+__global__ void __launch_bounds__(1024) k_ntt_mul_inv(MulArgs a) {
     extern __shared__ uint64_t su[];
     const uint64_t per_limb = (uint64_t)a.n_cols * a.n_blocks * 2;
     const uint64_t total = (uint64_t)a.Lq * per_limb;
@@ -722,18 +722,21 @@ icm_status icm_normalize(icm_ctx *c, const icm_scores *in, const uint8_t *dev_q_
     SL_TRY(set_smem(k_ntt_fwd, psm));
     SL_TRY(set_smem(k_ntt_mul_inv, psm));
     const unsigned per_sm = psm > 110000 ? 1 : (psm > 70000 ? 2 : 4);
+    // one polynomial per block in shared memory: the largest rings fit one block per SM, which
+    // then takes 1,024 threads to hide the latency of the butterflies' 64-bit products
+    const unsigned ntt_threads = psm > 70000 ? 1024 : 512;
     {
         FwdArgs a{};
         a.T = NT; a.N = N; a.Lq = Lq; a.per_limb = d3 * nb;
         a.src = mu; a.src_ls = (uint64_t)d3 * nb * N; a.src_ps = N;
         a.dst = mu; a.dst_ls = a.src_ls; a.dst_ps = N;
-        k_ntt_fwd<<<(unsigned)std::min<uint64_t>((uint64_t)Lq * d3 * nb, (uint64_t)sms * per_sm), 512, psm, st>>>(a);
+        k_ntt_fwd<<<(unsigned)std::min<uint64_t>((uint64_t)Lq * d3 * nb, (uint64_t)sms * per_sm), ntt_threads, psm, st>>>(a);
         SL_TRY(cudaGetLastError());
         FwdArgs b{};
         b.T = NT; b.N = N; b.Lq = Lq; b.per_limb = d3;
         b.src = in->dev; b.src_ls = (uint64_t)d3 * in->lay.M; b.src_ps = in->lay.M;
         b.dst = antt; b.dst_ls = (uint64_t)d3 * N; b.dst_ps = N;
-        k_ntt_fwd<<<(unsigned)std::min<uint64_t>((uint64_t)Lq * d3, (uint64_t)sms * per_sm), 512, psm, st>>>(b);
+        k_ntt_fwd<<<(unsigned)std::min<uint64_t>((uint64_t)Lq * d3, (uint64_t)sms * per_sm), ntt_threads, psm, st>>>(b);
         SL_TRY(cudaGetLastError());
     }
     // 4. products and inverse NTTs
@@ -741,7 +744,7 @@ icm_status icm_normalize(icm_ctx *c, const icm_scores *in, const uint8_t *dev_q_
         MulArgs a{};
         a.T = NT; a.N = N; a.Lq = Lq; a.n_cols = d3; a.n_blocks = nb; a.M = in->lay.M;
         a.scores = in->dev; a.a_ntt = antt; a.mu_ntt = mu; a.out = (uint64_t *)dev_out;
-        k_ntt_mul_inv<<<(unsigned)std::min<uint64_t>((uint64_t)Lq * d3 * nb * 2, (uint64_t)sms * per_sm), 512, psm, st>>>(a);
+        k_ntt_mul_inv<<<(unsigned)std::min<uint64_t>((uint64_t)Lq * d3 * nb * 2, (uint64_t)sms * per_sm), ntt_threads, psm, st>>>(a);
         SL_TRY(cudaGetLastError());
     }
     return ICM_OK;
