@@ -138,3 +138,58 @@ def test_trial_ranges_tile_the_run():
             assert rs[0][0] == 0 and sum(c for _, c in rs) == n
             assert all(rs[i][0] + rs[i][1] == rs[i + 1][0] for i in range(world - 1))
             assert max(c for _, c in rs) - min(c for _, c in rs) <= 1
+
+
+def _lib_rank_main(rank, world, port, n_db, out_q):
+    """One rank's host-side view of its shard through the library (no GPU work): context, primes,
+    CRT moduli, the shard's stored rows and bytes, and its per-step match footprint."""
+    from paper_2601_17561_gb300 import engine as E
+    from paper_2601_17561_gb300 import icm as C
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        p = dict(E.PAPER)
+        ctx = C.icm_ctx_create(C.icm_params(log_n_db=p["log_n_db"], log_n_q=p["log_n_q"], n_limbs=p["n_limbs"],
+                                            n_limbs_q=p["n_limbs_q"], prime_bits=p["prime_bits"], code_bits=12800,
+                                            d2=1 << 14, rho=31, fold_k=16, hamming_weight=512,
+                                            log2_delta=p["log2_delta"], noise_eta=21, seed=p["seed"]))
+        try:
+            nbytes, m_rows = C.icm_db_bytes(ctx, n_db)
+            view = (C.icm_ctx_primes(ctx, p["n_limbs"]), C.icm_ctx_crt_moduli(ctx), n_db, m_rows, nbytes,
+                    C.icm_query_ct_bytes(ctx, 32), shard.chunk_id(rank))
+        finally:
+            C.icm_ctx_destroy(ctx)
+        views = [None] * world
+        dist.all_gather_object(views, view)
+        if rank == 0:
+            out_q.put(views)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_ranks_library_host_view():
+    """The N > 1 path through the library's host side on two gloo ranks: every rank's context has
+    the same primes and CRT moduli (the query batch is common), each rank's shard of 7 x 2^14
+    templates is laid out as 7 full blocks (M = 8 x 2^14 rows, 206 GB at the paper shape), and the
+    query ciphertext a rank receives is the same size on every rank."""
+    from paper_2601_17561_gb300 import build as B
+    B.build()
+    n_db = 7 * (1 << 14)
+    ctx = mp.get_context("spawn")
+    out_q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_lib_rank_main, args=(r, WORLD, port, n_db, out_q)) for r in range(WORLD)]
+    for p in procs:
+        p.start()
+    views = out_q.get(timeout=300)
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    assert all(v[0] == views[0][0] and v[1] == views[0][1] for v in views)
+    assert len(views[0][1]) == 19
+    for v in views:
+        assert v[2] == n_db and v[3] == 8 * (1 << 14)
+        assert v[4] == 8 * v[3] * ((1 << 14) + (1 << 13)) * 8
+        assert v[5] == views[0][5] == 2 * 32 * 31 * ((1 << 14) + (1 << 13)) * 8
+    assert [v[6] for v in views] == list(range(WORLD))            # every shard its own a-part stream
