@@ -714,8 +714,8 @@ def main():
                          "roofline_frac": roof["frac"]}}
     for other in [x for x in args.compare_forms.split(",") if x and x != args.form]:
         tot, gm = timed_form(other, args.form_steps, max(args.form_warmup, 1))
-        fms = tot / args.form_steps
-        forms[other] = {"value": comps / (fms / 1e3), "ms_per_step": fms, "gemm_ms": statistics.mean(gm),
+        fms = shard.job_time_ms(tot, dist if ws > 1 else None, dev) / args.form_steps
+        forms[other] = {"value": shard.job_rate(ws, comps, fms), "ms_per_step": fms, "gemm_ms": statistics.mean(gm),
                         "steps": args.form_steps, "warmup": max(args.form_warmup, 1),
                         "roofline": form_roofline(other, statistics.mean(gm) / 1e3, None)}
 
