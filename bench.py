@@ -40,8 +40,8 @@ DTYPE = {"u64": "u64", "i8_digits": "int8", "i8_crt": "int8", "f16_crt": "f16"}
 # tiles does not depend on M, and the waves grow with row tiles x limbs x rounds); the int8 CRT
 # figure scales one 512-column round by 2 rounds.  Absent (null) for a kernel changed since.
 NCU_TRAFFIC = {
-    ("f16_crt", 2): 64 * (21_744_875_776 + 306_987_264),
-    ("i8_crt", 0): 2 * 64 * (12_206_364_000 + 161_416_192),
+    ("f16_crt", 2): 64 * (22_524_419_072 + 299_334_656),
+    ("i8_crt", 0): 2 * 64 * (12_100_983_040 + 155_742_464),
     ("u64", 0): 64 * (96_624_647_000 + 141_553_920),
 }
 

@@ -4,7 +4,7 @@
 // (the same residues held exactly as fp16, mma.sync m16n8k16 f16 -> f32; GB300 issues fp16 tensor
 // products at about four times its int8 rate).
 //
-// For r pairwise-coprime odd moduli m_i < 256 with product M > 2^9 K ((q-1)/2)^2:
+// For r pairwise-coprime odd moduli m_i < 256 with product M > 2^3 K ((q-1)/2)^2:
 //  phase 1 (one block per limb, modulus, 128-row tile and column tile): c_i = C mod m_i with
 //    C = sum_k a[k] b[k] over the centred residues a = A mod m_i, b = B mod m_i (|x| <= 127) of
 //    the centred lifts of A and B.  int8: int32 accumulation is exact (K 2^14 < 2^31).  fp16:
@@ -13,8 +13,8 @@
 //    leaves |x| <= 1.5 m_i because the rounded quotient may be off by one).  c_i goes to a byte
 //    scratch.
 //  phase 2 (one thread per output): C mod q = sum_i y_i (M/m_i mod q) - kappa (M mod q) with
-//    y_i = c_i (M/m_i)^-1 mod m_i and kappa = round(sum_i y_i / m_i) (|C| / M < 2^-9, so fp32
-//    decides kappa exactly).
+//    y_i = c_i (M/m_i)^-1 mod m_i and kappa = round(sum_i y_i / m_i) (|C| / M <= 2^-3 and the fp32
+//    sum is within 2^-14 of the exact one, so the rounding decides kappa exactly).
 //
 // Phase 1 tiling: 128 x BN tile per 256-thread block (2 x 4 warps, 64 x BN/4 each), K in slabs of
 // 32 values.  The database residues are formed on the fly from the canonical u64 (centred lift,
@@ -286,8 +286,8 @@ __global__ void __launch_bounds__(256) k_crt_combine(P2Args p) {
     const uint64_t col = idx / Mall, grow0 = idx % Mall;
     const uint8_t *Rl = p.R + (size_t)l * r * cnt + idx;
     // sum_i y_i W_i unreduced, over the 32-bit halves of W_i (y_i < 2^8, W_i < 2^60: each half-sum
-    // stays below r 2^40), reduced once at the end; F = sum_i y_i / m_i in fp32 (within 2^-9 of
-    // the integer kappa, so the rounding decides it exactly)
+    // stays below r 2^40), reduced once at the end; F = sum_i y_i / m_i in fp32 (within
+    // 2^-3 + 2^-14 of the integer kappa, so the rounding decides it exactly)
     uint64_t Alo[V], Ahi[V];
     float F[V];
 #pragma unroll

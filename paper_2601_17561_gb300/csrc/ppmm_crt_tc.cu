@@ -36,9 +36,10 @@
 // latency exposed (~30% slower).
 // Option SYNC (cooperative launch): the blocks start fetching the operands of their w-th tile
 // only once every block has issued all fetches of its (w-1)-th tile.  The persistent tiles run in
-// waves of 8 row tiles x 19 moduli; keeping the waves together keeps the database slabs (shared
-// by the 19 moduli of a row tile) and the query planes (shared by the row tiles of a modulus) in
-// L2 between their readers instead of letting the blocks drift apart over ~2,000 tiles.
+// waves of one tile per SM (8 to 9 row tiles x 18 moduli at the paper shape); keeping the waves
+// together keeps the database slabs (shared by the moduli of a row tile) and the query planes
+// (shared by the row tiles of a modulus) in L2 between their readers instead of letting the
+// blocks drift apart over ~2,000 tiles.
 //
 // Every wait is bounded by %globaltimer (a launch argument, default 2 s); on expiry the block
 // records ICM_DEV_TIMEOUT in the device status word, stops issuing work, waits (bounded) for its

@@ -12,10 +12,12 @@
 // is folded into the modular result R += (T mod q) (2^(8 s) mod q).
 //
 // CRT form (small-modulus RNS, as in the paper's own RNS of small moduli below 2^8): for r
-// pairwise-coprime odd moduli m_i < 256 whose product M exceeds 2 K ((q-1)/2)^2 by 2^8, one int8 GEMM
+// pairwise-coprime odd moduli m_i < 256 whose product M exceeds 2 K ((q-1)/2)^2 by 2^2, one int8 GEMM
 // per modulus on the centred residues of x mod m_i gives c_i = C mod m_i exactly (K (2^7)^2 < 2^31),
 // and C mod q = sum_i y_i (M/m_i mod q) - kappa (M mod q) with y_i = c_i (M/m_i)^-1 mod m_i and
-// kappa = round(sum_i y_i / m_i) (C / M lies within 2^-8 of zero, so fp32 decides kappa exactly).
+// kappa = round(sum_i y_i / m_i): sum_i y_i / m_i = kappa + C / M with |C / M| <= 2^-3, and its fp32
+// evaluation is off by less than 2^-14 (r <= 32 terms below 1, each with relative error <= 2^-23,
+// r additions below 2^5 with error <= 2^-19 each), so the rounding decides kappa exactly.
 // Residues of the database operand are formed on the fly from its digits with two dp4a.
 //
 // Base-p digit form (the paper's own modulus family, Section 6.2.2: Q = prod p^2): for q = p^2
@@ -468,8 +470,8 @@ uint64_t shoup_h(uint64_t w, uint64_t q) { return (uint64_t)(((u128)w << 64) / q
 uint32_t crt_moduli(const uint64_t *q, size_t nq, uint64_t K, int (&mods)[ICM_MAX_MODULI]) {
     uint64_t qmax = 0;
     for (size_t i = 0; i < nq; ++i) qmax = q[i] > qmax ? q[i] : qmax;
-    // |C| <= K ((qmax-1)/2)^2; need log2 M >= 1 + log2|C| + 8 (kappa margin)
-    const double need = 1.0 + std::log2((double)(K ? K : 1)) + 2.0 * std::log2((double)((qmax - 1) / 2 + 1)) + 8.0;
+    // |C| <= K ((qmax-1)/2)^2; need log2 M >= 1 + log2|C| + 2 (kappa margin: |C| / M <= 2^-3)
+    const double need = 1.0 + std::log2((double)(K ? K : 1)) + 2.0 * std::log2((double)((qmax - 1) / 2 + 1)) + 2.0;
     uint32_t n = 0;
     double have = 0;
     for (int v = 255; v >= 3 && have < need && n < ICM_MAX_MODULI; v -= 2) {

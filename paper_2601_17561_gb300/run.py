@@ -5,7 +5,7 @@
 Workloads: tiny (4 eyes x 256 codes, ring 2^12, 3 primes < 2^50), mid (32 eyes x 2,000 codes,
 same ring and primes: about 3 GB on the device, sized for profiler captures), slice (32 eyes x
 4,096 codes with the paper's query side -- N_q = 2^13, d = 2^14, K = 24,576, primes < 2^60, so
-19 CRT moduli -- but N_db = 2^12 and 2 primes: M = 8,192 rows, 3.2 GB, the paper's tile shape
+18 CRT moduli -- but N_db = 2^12 and 2 primes: M = 8,192 rows, 3.2 GB, the paper's tile shape
 and wave order at a profiler-sized scale), paper (32 eyes x 114,688 codes, N_db = 2^14,
 N_q = 2^13, 8 primes < 2^60), slots (a slot-encoded database of 1,024 templates in one block of
 N_db = 2^11, the paper's query side for 32 eyes, 4 primes < 2^60: 3.2 GB).  Each pass prepares the

@@ -193,6 +193,45 @@ def test_ppmm_extremes(form, kind):
         assert np.all(got[l] == (xc[l] * xc[l] * K) % q_l)
 
 
+def _crt_edge_depth(q):
+    """Even K as deep as the CRT forms allow before the small-modulus count grows: the product M
+    of the greedy moduli (odd, pairwise coprime, from 255 down) covering 2^3 K ((q-1)/2)^2 stays
+    that of K = 2^14, so |C| / M for operands at the largest centred lift approaches 1/8, the
+    recombination's design limit."""
+    import math
+    h = (max(q) - 1) // 2
+    need = 8 * (1 << 14) * h * h
+    mods, M = [], 1
+    for v in range(255, 2, -2):
+        if M > need:
+            break
+        if all(math.gcd(v, m) == 1 for m in mods):
+            mods.append(v)
+            M *= v
+    K = (M // (8 * h * h)) * 63 // 64
+    return min(K - K % 2, 131070), len(mods)
+
+
+@pytest.mark.parametrize("form", ["i8_crt", "f16_crt"])
+@pytest.mark.parametrize("sign", [1, -1])
+def test_ppmm_crt_range_edge(form, sign):
+    """Every operand at the largest centred lift (q-1)/2, against +-(q-1)/2, at a depth K where
+    |C| / M is close to 1/8 (58-bit primes, 17 moduli): C = +-K ((q-1)/2)^2 is recombined exactly
+    (the fp32 quotient of the recombination still rounds to the right integer)."""
+    B.build()
+    q = O.primes(58, 2)
+    K, r = _crt_edge_depth(q)
+    assert r == 17 and K > 1 << 15
+    xa = [(q_l - 1) // 2 for q_l in q]
+    xb = [sign * x for x in xa]
+    A = np.stack([np.full((70, K), x % q_l, np.uint64) for x, q_l in zip(xa, q)])
+    Bm = np.stack([np.full((9, K), x % q_l, np.uint64) for x, q_l in zip(xb, q)])
+    got = E.ppmm(form, q, torch.from_numpy(A.view(np.int64)).cuda(),
+                 torch.from_numpy(Bm.view(np.int64)).cuda()).cpu().numpy().view(np.uint64)
+    for l, q_l in enumerate(q):
+        assert np.all(got[l] == (xa[l] * xb[l] * K) % q_l)
+
+
 @pytest.mark.parametrize("variant", [1, 2, 3])
 def test_ccmm_tcgen05_variant_bit_exact(tiny, gpu_run, variant):
     """Every tcgen05 kernel variant of the fp16 CRT form (tensor-memory accumulators, one modulus
@@ -312,18 +351,19 @@ def test_ccmm_tcgen05_launch_rounds(tiny, n_eyes):
 
 
 def test_ccmm_tcgen05_odd_modulus_count():
-    """54-bit primes give 17 CRT moduli (an odd count, so the waves of persistent tiles do not
+    """56-bit primes give 17 CRT moduli (an odd count, so the waves of persistent tiles do not
     split evenly over row tiles): residues of the tcgen05 variants equal the mma.sync variant's
     everywhere and the oracle's product on sampled rows."""
     from paper_2601_17561_gb300 import icm as C
     prm = dict(O.TINY)
-    prm.update(prime_bits=54, seed=5)
+    prm.update(prime_bits=56, seed=5)
     P = O.Params(**prm)
     W = synth.make_workload(n_eyes=8, n_db=140, seed=12, planted_frac=0.05)
     eprm = dict(E.TINY)
-    eprm.update(prime_bits=54, seed=5)
+    eprm.update(prime_bits=56, seed=5)
     eng = E.Engine(**eprm).keygen()
     assert eng.primes == P.q
+    assert len(C.icm_ctx_crt_moduli(eng.ctx)) == 17
     db = eng.encrypt_db(W.db_codes, W.db_masks)
     ct = eng.encrypt_query(W.q_codes, W.q_masks, W.eye_ids)
     res = {}

@@ -58,7 +58,8 @@ def test_primes_agree_with_oracle_rule(lib, cfg):
 def test_crt_moduli_cover_the_product_range(lib, cfg):
     """The CRT forms' small moduli: odd, below 2^8, pairwise coprime, and their product exceeds
     twice the largest |sum of K centred residue products| (so the CRT value is the exact integer),
-    with at least 8 bits to spare."""
+    with at least 2 bits to spare (|C| / M <= 1/8, against an fp32 error below 2^-14 in the
+    recombination's rounded quotient)."""
     import math
     ctx = C.icm_ctx_create(_params(**cfg))
     try:
@@ -70,11 +71,11 @@ def test_crt_moduli_cover_the_product_range(lib, cfg):
     assert all(m % 2 == 1 and 3 <= m < 256 for m in mods)
     assert all(math.gcd(a, b) == 1 for i, a in enumerate(mods) for b in mods[i + 1:])
     bound = K * ((max(q) - 1) // 2) ** 2
-    assert math.prod(mods) > 2 * bound * 256
+    assert math.prod(mods) > 2 * bound * 4
     # greedy from 255 down: dropping the smallest modulus no longer covers the range with margin
-    assert math.prod(mods[:-1]) < 2 * (bound + 1) * 256 * 2
+    assert math.prod(mods[:-1]) < 2 * (bound + 1) * 4 * 2
     if cfg is O.PAPER:
-        assert len(mods) == 19
+        assert len(mods) == 18
 
 
 @pytest.mark.parametrize("cfg", [O.TINY, O.PAPER])

@@ -187,7 +187,7 @@ def test_two_ranks_library_host_view():
         p.join(timeout=120)
         assert p.exitcode == 0
     assert all(v[0] == views[0][0] and v[1] == views[0][1] for v in views)
-    assert len(views[0][1]) == 19
+    assert len(views[0][1]) == 18
     for v in views:
         assert v[2] == n_db and v[3] == 8 * (1 << 14)
         assert v[4] == 8 * v[3] * ((1 << 14) + (1 << 13)) * 8
