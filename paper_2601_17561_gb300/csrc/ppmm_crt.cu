@@ -12,9 +12,10 @@
 //    is reduced modulo m_i every 1024 columns of K (1024 * 127^2 + 1.5 * 255 < 2^24; a reduction
 //    leaves |x| <= 1.5 m_i because the rounded quotient may be off by one).  c_i goes to a byte
 //    scratch.
-//  phase 2 (one thread per output): C mod q = sum_i y_i (M/m_i mod q) - kappa (M mod q) with
-//    y_i = c_i (M/m_i)^-1 mod m_i and kappa = round(sum_i y_i / m_i) (|C| / M <= 2^-3 and the fp32
-//    sum is within 2^-14 of the exact one, so the rounding decides kappa exactly).
+//  phase 2 (one thread per output): C mod q = sum_i x_i (M/m_i mod q) - kappa (M mod q) with
+//    x_i = c_i ((M/m_i)^-1 mod m_i), unreduced, and kappa = round(sum_i x_i / m_i) (|C| / M <= 2^-3
+//    and the 32.32 fixed-point sum is within 2^-12 of the exact one, so the rounding decides kappa
+//    exactly).
 //
 // Phase 1 tiling: 128 x BN tile per 256-thread block (2 x 4 warps, 64 x BN/4 each), K in slabs of
 // 32 values.  The database residues are formed on the fly from the canonical u64 (centred lift,
@@ -270,10 +271,12 @@ struct P2Args {
     icm::I8Consts k;
 };
 
-// Phase 2: C mod q = sum_i y_i (M/m_i mod q) - kappa (M mod q) with y_i = c_i (M/m_i)^-1 mod m_i
-// (one multiply-high division: c_i yinv_i < 2^16) and kappa = round(sum_i y_i / m_i).  Each thread
-// takes V consecutive rows of one column (V = 4: one 4-byte load per modulus plane, when the row
-// count keeps those words aligned).
+// Phase 2: C mod q = sum_i x_i (M/m_i mod q) - kappa (M mod q) with x_i = c_i ((M/m_i)^-1 mod m_i)
+// left unreduced (< 2^16: x_i = y_i mod m_i is all the sum needs, so sum_i x_i M/m_i is still
+// C + kappa M) and kappa = round(sum_i x_i / m_i) in 32.32 fixed point: T = sum_i x_i R_i with
+// R_i = round(2^32 / m_i) is 2^32 (kappa + C / M) within r 2^15, and |C| / M <= 1/8, so
+// kappa = (T + 2^31) >> 32 exactly.  Each thread takes V consecutive rows of one column (V = 4:
+// one 4-byte load per modulus plane, when the row count keeps those words aligned).
 template <int V>
 __global__ void __launch_bounds__(256) k_crt_combine(P2Args p) {
     const uint32_t l = blockIdx.y;
@@ -285,25 +288,21 @@ __global__ void __launch_bounds__(256) k_crt_combine(P2Args p) {
     if (idx >= cnt) return;
     const uint64_t col = idx / Mall, grow0 = idx % Mall;
     const uint8_t *Rl = p.R + (size_t)l * r * cnt + idx;
-    // sum_i y_i W_i unreduced, over the 32-bit halves of W_i (y_i < 2^8, W_i < 2^60: each half-sum
-    // stays below r 2^40), reduced once at the end; F = sum_i y_i / m_i in fp32 (within
-    // 2^-3 + 2^-14 of the integer kappa, so the rounding decides it exactly)
-    uint64_t Alo[V], Ahi[V];
-    float F[V];
+    // sum_i x_i W_i over the 32-bit halves of W_i (x_i < 2^16, W_i < 2^60: each half-sum stays
+    // below r 2^48), reduced once at the end; T = sum_i x_i R_i (R_i < 2^31: below r 2^47)
+    uint64_t Alo[V], Ahi[V], T[V];
 #pragma unroll
-    for (int e = 0; e < V; ++e) { Alo[e] = 0; Ahi[e] = 0; F[e] = 0.f; }
+    for (int e = 0; e < V; ++e) { Alo[e] = 0; Ahi[e] = 0; T[e] = 0; }
     for (uint32_t i = 0; i < r; ++i) {
         const uint32_t w = V == 4 ? *reinterpret_cast<const uint32_t *>(Rl + (size_t)i * cnt) : Rl[(size_t)i * cnt];
-        const uint32_t yinv = (uint32_t)p.k.yinv[i], m = (uint32_t)p.k.mod[i], magic = p.k.magic[i];
+        const uint32_t yinv = (uint32_t)p.k.yinv[i], ri = p.k.r32[i];
         const uint32_t wlo = (uint32_t)p.k.W[l][i], whi = (uint32_t)(p.k.W[l][i] >> 32);
-        const float inv_m = p.k.inv_m[i];
 #pragma unroll
         for (int e = 0; e < V; ++e) {
             const uint32_t x = ((w >> (8 * e)) & 0xFF) * yinv;
-            const uint32_t y = x - __umulhi(x, magic) * m;
-            Alo[e] += (uint64_t)y * wlo;
-            Ahi[e] += (uint64_t)y * whi;
-            F[e] += (__int_as_float(0x4B000000u | y) - 8388608.f) * inv_m;     // (float)y, exact for y < 2^23
+            Alo[e] += (uint64_t)x * wlo;
+            Ahi[e] += (uint64_t)x * whi;
+            T[e] += (uint64_t)x * ri;
         }
     }
     const uint64_t r64 = p.k.r64[l], p32 = p.k.pw8[l][4], p32s = p.k.pw8s[l][4];       // 2^32 mod q
@@ -314,7 +313,7 @@ __global__ void __launch_bounds__(256) k_crt_combine(P2Args p) {
         while (c + 1 < p.tab.n && grow >= p.tab.row0[c + 1]) ++c;
         const uint64_t row = grow - p.tab.row0[c], M = p.tab.M[c];
         const uint64_t S = add_mod(reduce64(Alo[e], q, r64), mulmod_shoup(reduce64(Ahi[e], q, r64), p32, p32s, q), q);
-        const uint64_t kappa = (uint64_t)__float2int_rn(F[e]);
+        const uint64_t kappa = (T[e] + (1ull << 31)) >> 32;
         p.tab.C[c][((size_t)l * p.N + p.n0 + col) * M + row] = sub_mod(S, mulmod_shoup(kappa, p.k.Mq[l], p.k.Mqs[l], q), q);
     }
 }

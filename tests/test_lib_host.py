@@ -58,7 +58,7 @@ def test_primes_agree_with_oracle_rule(lib, cfg):
 def test_crt_moduli_cover_the_product_range(lib, cfg):
     """The CRT forms' small moduli: odd, below 2^8, pairwise coprime, and their product exceeds
     twice the largest |sum of K centred residue products| (so the CRT value is the exact integer),
-    with at least 2 bits to spare (|C| / M <= 1/8, against an fp32 error below 2^-14 in the
+    with at least 2 bits to spare (|C| / M <= 1/8, against a fixed-point error below 2^-12 in the
     recombination's rounded quotient)."""
     import math
     ctx = C.icm_ctx_create(_params(**cfg))
