@@ -79,6 +79,32 @@ def test_crt_moduli_cover_the_product_range(lib, cfg):
 
 
 @pytest.mark.parametrize("cfg", [O.TINY, O.PAPER])
+def test_crt_recombination_rule(lib, cfg):
+    """The recombination's rule, in exact integers over the library's moduli: with
+    x_i = c_i ((M/m_i)^-1 mod m_i) left unreduced, sum_i x_i (M/m_i) - kappa M recovers every
+    centred C with |C| <= M/8 when kappa is rounded from the 32.32 fixed-point sum
+    sum_i x_i round(2^32 / m_i) (the margin the moduli are chosen with), including C at +-M/8."""
+    import math
+    ctx = C.icm_ctx_create(_params(**cfg))
+    try:
+        mods = C.icm_ctx_crt_moduli(ctx)
+    finally:
+        C.icm_ctx_destroy(ctx)
+    M = math.prod(mods)
+    yinv = [pow((M // m) % m, -1, m) for m in mods]
+    r32 = [((1 << 32) + m // 2) // m for m in mods]
+    rng = np.random.default_rng(11)
+    cases = [M // 8, -(M // 8), 0, 1, -1] + [int(v) for v in rng.integers(-(1 << 62), 1 << 62, size=300)]
+    cases += [(M // 8) * int(f) // 1000 for f in rng.integers(-1000, 1001, size=300)]
+    for Cv in cases:
+        x = [(Cv % m) * yi for m, yi in zip(mods, yinv)]
+        T = sum(xi * ri for xi, ri in zip(x, r32))
+        assert T < 1 << 64
+        kappa = (T + (1 << 31)) >> 32
+        assert sum(xi * (M // m) for xi, m in zip(x, mods)) - kappa * M == Cv
+
+
+@pytest.mark.parametrize("cfg", [O.TINY, O.PAPER])
 def test_slot_database_size(lib, cfg):
     """A slot-encoded chunk holds N_db/2 templates per block (one per slot), all blocks full:
     M = N_db + ceil(n_db / (N_db/2)) N_db rows of L x K words."""
