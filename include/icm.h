@@ -108,9 +108,11 @@ icm_status icm_ctx_create(const icm_params *p, icm_ctx **out);
 void icm_ctx_destroy(icm_ctx *ctx);
 /* Copy the primes (n >= n_limbs values) to host memory. */
 icm_status icm_ctx_primes(const icm_ctx *ctx, uint64_t *primes, size_t n);
-/* The small moduli of the CRT forms (Section 6.2.2's RNS of moduli below 2^8): *n_moduli receives
- * their count r (the tensor-core products per modular multiply-add), and the first min(cap, r)
- * moduli go to `moduli` (host array, may be NULL with cap 0).  ICM_EBOUND if the CRT forms are
+/* The small moduli of the CRT forms (Section 6.2.2's RNS of moduli below 2^8): the largest
+ * pairwise-coprime odd integers below 256, as many as make their product exceed
+ * 2^3 K ((q_max - 1)/2)^2 (18 for primes below 2^60 at K = 24,576).  *n_moduli receives their
+ * count r (the tensor-core products per modular multiply-add), and the first min(cap, r) moduli
+ * go to `moduli` (host array, may be NULL with cap 0).  ICM_EBOUND if the CRT forms are
  * unavailable for this context's primes and K. */
 icm_status icm_ctx_crt_moduli(const icm_ctx *ctx, int32_t *moduli, size_t cap, size_t *n_moduli);
 
