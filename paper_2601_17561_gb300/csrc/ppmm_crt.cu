@@ -12,10 +12,9 @@
 //    is reduced modulo m_i every 1024 columns of K (1024 * 127^2 + 1.5 * 255 < 2^24; a reduction
 //    leaves |x| <= 1.5 m_i because the rounded quotient may be off by one).  c_i goes to a byte
 //    scratch.
-//  phase 2 (one thread per output): C mod q = sum_i x_i (M/m_i mod q) - kappa (M mod q) with
-//    x_i = c_i ((M/m_i)^-1 mod m_i), unreduced, and kappa = round(sum_i x_i / m_i) (|C| / M <= 2^-3
-//    and the 32.32 fixed-point sum is within 2^-12 of the exact one, so the rounding decides kappa
-//    exactly).
+//  phase 2 (one thread per output): C mod q = sum_i c_i (y_i M/m_i mod q) - kappa (M mod q) with
+//    y_i = (M/m_i)^-1 mod m_i and kappa = round(sum_i c_i y_i / m_i) (|C| / M <= 2^-3 and the
+//    fixed-point sum is within 2^-7 of the exact one, so the rounding decides kappa exactly).
 //
 // Phase 1 tiling: 128 x BN tile per 256-thread block (2 x 4 warps, 64 x BN/4 each), K in slabs of
 // 32 values.  The database residues are formed on the fly from the canonical u64 (centred lift,
@@ -271,12 +270,14 @@ struct P2Args {
     icm::I8Consts k;
 };
 
-// Phase 2: C mod q = sum_i x_i (M/m_i mod q) - kappa (M mod q) with x_i = c_i ((M/m_i)^-1 mod m_i)
-// left unreduced (< 2^16: x_i = y_i mod m_i is all the sum needs, so sum_i x_i M/m_i is still
-// C + kappa M) and kappa = round(sum_i x_i / m_i) in 32.32 fixed point: T = sum_i x_i R_i with
-// R_i = round(2^32 / m_i) is 2^32 (kappa + C / M) within r 2^15, and |C| / M <= 1/8, so
-// kappa = (T + 2^31) >> 32 exactly.  Each thread takes V consecutive rows of one column (V = 4:
-// one 4-byte load per modulus plane, when the row count keeps those words aligned).
+// Phase 2: with y_i = (M/m_i)^-1 mod m_i, sum_i c_i y_i (M/m_i) = C + kappa M for an integer kappa
+// (each term's residue modulo m_i is c_i, and modulo every other m_j it is 0), so
+// C mod q = sum_i c_i Wy_i - kappa (M mod q) with the constants Wy_i = y_i (M/m_i) mod q, and
+// kappa = round(sum_i c_i y_i / m_i) in fixed point: T = sum_i c_i R_i with
+// R_i = round(2^19 y_i / m_i) < 2^19 is 2^19 (kappa + C / M) within r 2^7 (c_i < 2^8), and
+// |C| / M <= 1/8, so kappa = (T + 2^18) >> 19 exactly (T < r 2^27 fits 32 bits).  Each thread
+// takes V consecutive rows of one column (V = 4: one 4-byte load per modulus plane, when the row
+// count keeps those words aligned).
 template <int V>
 __global__ void __launch_bounds__(256) k_crt_combine(P2Args p) {
     const uint32_t l = blockIdx.y;
@@ -288,21 +289,22 @@ __global__ void __launch_bounds__(256) k_crt_combine(P2Args p) {
     if (idx >= cnt) return;
     const uint64_t col = idx / Mall, grow0 = idx % Mall;
     const uint8_t *Rl = p.R + (size_t)l * r * cnt + idx;
-    // sum_i x_i W_i over the 32-bit halves of W_i (x_i < 2^16, W_i < 2^60: each half-sum stays
-    // below r 2^48), reduced once at the end; T = sum_i x_i R_i (R_i < 2^31: below r 2^47)
-    uint64_t Alo[V], Ahi[V], T[V];
+    // sum_i c_i Wy_i over the 32-bit halves of Wy_i (c_i < 2^8, Wy_i < 2^60: each half-sum stays
+    // below r 2^40), reduced once at the end
+    uint64_t Alo[V], Ahi[V];
+    uint32_t T[V];
 #pragma unroll
     for (int e = 0; e < V; ++e) { Alo[e] = 0; Ahi[e] = 0; T[e] = 0; }
     for (uint32_t i = 0; i < r; ++i) {
         const uint32_t w = V == 4 ? *reinterpret_cast<const uint32_t *>(Rl + (size_t)i * cnt) : Rl[(size_t)i * cnt];
-        const uint32_t yinv = (uint32_t)p.k.yinv[i], ri = p.k.r32[i];
-        const uint32_t wlo = (uint32_t)p.k.W[l][i], whi = (uint32_t)(p.k.W[l][i] >> 32);
+        const uint32_t ri = p.k.r19[i];
+        const uint32_t wlo = (uint32_t)p.k.Wy[l][i], whi = (uint32_t)(p.k.Wy[l][i] >> 32);
 #pragma unroll
         for (int e = 0; e < V; ++e) {
-            const uint32_t x = ((w >> (8 * e)) & 0xFF) * yinv;
-            Alo[e] += (uint64_t)x * wlo;
-            Ahi[e] += (uint64_t)x * whi;
-            T[e] += (uint64_t)x * ri;
+            const uint32_t c = (w >> (8 * e)) & 0xFF;
+            Alo[e] += (uint64_t)c * wlo;
+            Ahi[e] += (uint64_t)c * whi;
+            T[e] += c * ri;
         }
     }
     const uint64_t r64 = p.k.r64[l], p32 = p.k.pw8[l][4], p32s = p.k.pw8s[l][4];       // 2^32 mod q
@@ -313,7 +315,7 @@ __global__ void __launch_bounds__(256) k_crt_combine(P2Args p) {
         while (c + 1 < p.tab.n && grow >= p.tab.row0[c + 1]) ++c;
         const uint64_t row = grow - p.tab.row0[c], M = p.tab.M[c];
         const uint64_t S = add_mod(reduce64(Alo[e], q, r64), mulmod_shoup(reduce64(Ahi[e], q, r64), p32, p32s, q), q);
-        const uint64_t kappa = (T[e] + (1ull << 31)) >> 32;
+        const uint64_t kappa = (T[e] + (1u << 18)) >> 19;
         p.tab.C[c][((size_t)l * p.N + p.n0 + col) * M + row] = sub_mod(S, mulmod_shoup(kappa, p.k.Mq[l], p.k.Mqs[l], q), q);
     }
 }
@@ -437,7 +439,9 @@ static I8Consts limb_slice(const I8Consts &k, uint32_t l0, uint32_t n) {
         const uint32_t f = l0 + l;
         s.q[l] = k.q[f]; s.r64[l] = k.r64[f];
         for (int t = 0; t < 15; ++t) { s.pw8[l][t] = k.pw8[f][t]; s.pw8s[l][t] = k.pw8s[f][t]; }
-        for (uint32_t i = 0; i < ICM_MAX_MODULI; ++i) { s.W[l][i] = k.W[f][i]; s.Ws[l][i] = k.Ws[f][i]; }
+        for (uint32_t i = 0; i < ICM_MAX_MODULI; ++i) {
+            s.W[l][i] = k.W[f][i]; s.Ws[l][i] = k.Ws[f][i]; s.Wy[l][i] = k.Wy[f][i];
+        }
         s.Mq[l] = k.Mq[f]; s.Mqs[l] = k.Mqs[f];
         s.pd[l] = k.pd[f]; s.inv_p[l] = k.inv_p[f];
     }

@@ -14,10 +14,11 @@
 // CRT form (small-modulus RNS, as in the paper's own RNS of small moduli below 2^8): for r
 // pairwise-coprime odd moduli m_i < 256 whose product M exceeds 2 K ((q-1)/2)^2 by 2^2, one int8 GEMM
 // per modulus on the centred residues of x mod m_i gives c_i = C mod m_i exactly (K (2^7)^2 < 2^31),
-// and C mod q = sum_i x_i (M/m_i mod q) - kappa (M mod q) with x_i = c_i ((M/m_i)^-1 mod m_i) and
-// kappa = round(sum_i x_i / m_i): sum_i x_i / m_i = kappa + C / M with |C / M| <= 2^-3, evaluated
-// in 32.32 fixed point with constants round(2^32 / m_i), off by at most r 2^15 / 2^32 < 2^-12
-// (x_i < 2^16, r <= 32), so the rounding decides kappa exactly.
+// and C mod q = sum_i c_i (y_i (M/m_i) mod q) - kappa (M mod q) with y_i = (M/m_i)^-1 mod m_i and
+// kappa = round(sum_i c_i y_i / m_i): sum_i c_i y_i (M/m_i) = C + kappa M, and
+// sum_i c_i y_i / m_i = kappa + C / M with |C / M| <= 2^-3, evaluated in fixed point with
+// constants round(2^19 y_i / m_i), off by at most r 2^7 / 2^19 < 2^-7 (c_i < 2^8, r <= 24), so
+// the rounding decides kappa exactly.
 // Residues of the database operand are formed on the fly from its digits with two dp4a.
 //
 // Base-p digit form (the paper's own modulus family, Section 6.2.2: Q = prod p^2): for q = p^2
@@ -536,7 +537,6 @@ bool make_i8_consts(int form, const uint64_t *q, size_t nq, uint64_t K, I8Consts
         k.wlo[i] = (int32_t)((uint32_t)(uint8_t)w[0] | ((uint32_t)(uint8_t)w[1] << 8) | ((uint32_t)(uint8_t)w[2] << 16) | ((uint32_t)(uint8_t)w[3] << 24));
         k.whi[i] = (int32_t)((uint32_t)(uint8_t)w[4] | ((uint32_t)(uint8_t)w[5] << 8) | ((uint32_t)(uint8_t)w[6] << 16) | ((uint32_t)(uint8_t)w[7] << 24));
         k.inv_m[i] = 1.0f / (float)m;
-        k.r32[i] = (uint32_t)(((1ull << 32) + (uint64_t)m / 2) / (uint64_t)m);
         const int h = m / 2;
         k.cbias[i] = m * ((131072 + m - 1) / m) + h;
         k.magic[i] = (uint32_t)(((1ull << 32) + (uint64_t)m - 1) / (uint64_t)m);
@@ -546,11 +546,13 @@ bool make_i8_consts(int form, const uint64_t *q, size_t nq, uint64_t K, I8Consts
         uint64_t hat = 1;
         for (uint32_t j = 0; j < nm; ++j) if (j != i) hat = hat * (uint64_t)mods[j] % (uint64_t)m;
         k.yinv[i] = (int32_t)inv_h((int64_t)hat, m);
+        k.r19[i] = (uint32_t)((((uint64_t)k.yinv[i] << 19) + (uint64_t)m / 2) / (uint64_t)m);
         for (size_t l = 0; l < nq; ++l) {
             uint64_t W = 1 % q[l];
             for (uint32_t j = 0; j < nm; ++j) if (j != i) W = mulmod_h(W, (uint64_t)mods[j], q[l]);
             k.W[l][i] = W;
             k.Ws[l][i] = shoup_h(W, q[l]);
+            k.Wy[l][i] = mulmod_h((uint64_t)k.yinv[i], W, q[l]);
         }
     }
     for (size_t l = 0; l < nq; ++l) {

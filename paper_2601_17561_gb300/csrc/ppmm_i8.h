@@ -16,15 +16,16 @@ struct I8Consts {
     // digit form: 2^(8 s) mod q_l for shifts s = 0..14, with Shoup companions
     uint64_t pw8[ICM_MAX_LIMBS][15], pw8s[ICM_MAX_LIMBS][15];
     // CRT form: moduli, packed centred constants 256^t mod m (t = 0..3 and 4..7), 1/m,
-    // round(2^32 / m), (M/m_i)^-1 mod m_i, (M/m_i) mod q_l and M mod q_l with Shoup companions
+    // y_i = (M/m_i)^-1 mod m_i and round(2^19 y_i / m_i), (M/m_i) mod q_l, y_i (M/m_i) mod q_l,
+    // M mod q_l with Shoup companions
     int32_t mod[ICM_MAX_MODULI], wlo[ICM_MAX_MODULI], whi[ICM_MAX_MODULI], yinv[ICM_MAX_MODULI];
     float inv_m[ICM_MAX_MODULI];
-    uint32_t r32[ICM_MAX_MODULI];
+    uint32_t r19[ICM_MAX_MODULI];
     // integer residue conversion of the tcgen05 path: dp4a bias c = m ceil(2^17 / m) + h with
     // h = floor(m / 2), division magic ceil(2^32 / m), and the f16x2 bits of -(1024 + h)
     int32_t cbias[ICM_MAX_MODULI];
     uint32_t magic[ICM_MAX_MODULI], hneg2[ICM_MAX_MODULI];
-    uint64_t W[ICM_MAX_LIMBS][ICM_MAX_MODULI], Ws[ICM_MAX_LIMBS][ICM_MAX_MODULI];
+    uint64_t W[ICM_MAX_LIMBS][ICM_MAX_MODULI], Ws[ICM_MAX_LIMBS][ICM_MAX_MODULI], Wy[ICM_MAX_LIMBS][ICM_MAX_MODULI];
     uint64_t Mq[ICM_MAX_LIMBS], Mqs[ICM_MAX_LIMBS];
     // p^2 form: q_l = pd_l^2, digit base pd_l and 1 / pd_l (pw8[l][0..1] hold 1 and pd_l)
     int32_t pd[ICM_MAX_LIMBS];

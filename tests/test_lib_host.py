@@ -81,9 +81,9 @@ def test_crt_moduli_cover_the_product_range(lib, cfg):
 @pytest.mark.parametrize("cfg", [O.TINY, O.PAPER])
 def test_crt_recombination_rule(lib, cfg):
     """The recombination's rule, in exact integers over the library's moduli: with
-    x_i = c_i ((M/m_i)^-1 mod m_i) left unreduced, sum_i x_i (M/m_i) - kappa M recovers every
-    centred C with |C| <= M/8 when kappa is rounded from the 32.32 fixed-point sum
-    sum_i x_i round(2^32 / m_i) (the margin the moduli are chosen with), including C at +-M/8."""
+    y_i = (M/m_i)^-1 mod m_i, sum_i c_i y_i (M/m_i) - kappa M recovers every centred C with
+    |C| <= M/8 (the margin the moduli are chosen with, C at +-M/8 included) when kappa is rounded
+    from the fixed-point sum sum_i c_i round(2^19 y_i / m_i), which stays below 2^32."""
     import math
     ctx = C.icm_ctx_create(_params(**cfg))
     try:
@@ -92,16 +92,16 @@ def test_crt_recombination_rule(lib, cfg):
         C.icm_ctx_destroy(ctx)
     M = math.prod(mods)
     yinv = [pow((M // m) % m, -1, m) for m in mods]
-    r32 = [((1 << 32) + m // 2) // m for m in mods]
+    r19 = [((y << 19) + m // 2) // m for m, y in zip(mods, yinv)]
     rng = np.random.default_rng(11)
     cases = [M // 8, -(M // 8), 0, 1, -1] + [int(v) for v in rng.integers(-(1 << 62), 1 << 62, size=300)]
     cases += [(M // 8) * int(f) // 1000 for f in rng.integers(-1000, 1001, size=300)]
     for Cv in cases:
-        x = [(Cv % m) * yi for m, yi in zip(mods, yinv)]
-        T = sum(xi * ri for xi, ri in zip(x, r32))
-        assert T < 1 << 64
-        kappa = (T + (1 << 31)) >> 32
-        assert sum(xi * (M // m) for xi, m in zip(x, mods)) - kappa * M == Cv
+        c = [Cv % m for m in mods]
+        T = sum(ci * ri for ci, ri in zip(c, r19))
+        assert T < 1 << 32
+        kappa = (T + (1 << 18)) >> 19
+        assert sum(ci * yi * (M // m) for ci, yi, m in zip(c, yinv, mods)) - kappa * M == Cv
 
 
 @pytest.mark.parametrize("cfg", [O.TINY, O.PAPER])
